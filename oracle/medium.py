@@ -1,0 +1,192 @@
+"""Per-voxel FP64 coefficient arrays in the paper's form (test infrastructure only).
+
+* K = rho c^2 and the p update factor K dt (Eq. wave2 with kappa = 1/K);
+* face density: arithmetic mean of the two cells that share the face (the last
+  face of a non-periodic axis takes the cell's own rho);
+* recursion coefficients per mechanism (Eqs. relaxation_a, relaxation_b):
+      b = exp(-(d/kappa + alpha) dt),  a = d / (kappa (d + kappa alpha)) (b - 1);
+* a velocity point v_d[i] (at i + 1/2 along d) takes the relaxation class of
+  cell i, its lower neighbour;
+* absorbing boundary: one more mechanism per direction, same Debye form, in a
+  layer of L_T transition + L_B absorbing cells on every side.  The maps of
+  that layer are inherited from the nearest interior cell (the adaptive PML
+  of Sec. 4.6); the tissue mechanisms continue unchanged through it.
+  Reading of the profile (the paper defers it to its Fullwave 2 reference):
+  depth s [cells] from the inner edge of the layer,
+      d(s) = 0.1 d_max (s/L_T)^2                   for s <= L_T,
+      d(s) = d_max (0.1 + 0.9 ((s-L_T)/L_B)^2)     for s >  L_T,
+      (L_T = 0: d(s) = d_max (s/L_B)^2),
+      d_max = -3 c_max ln(R0) / (2 L_B dx),  R0 = 1e-5,
+      alpha(s) = pi f0 (1 - s/(L_T+L_B)),
+  and kappa of the mechanism = the tissue kappa of the point's stretch.
+* time step from a CFL number: dt = CFL dx / max(c / sqrt(kappa_1 kappa_2)).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from .fit import RelaxParams
+
+
+def class_table(params):
+    """Stack a list of RelaxParams into arrays [n_class] / [n_class, N]."""
+    n = params[0].n_mech
+    for p in params:
+        assert p.n_mech == n
+    return dict(
+        kappa1=np.array([p.kappa1 for p in params], dtype=np.float64),
+        kappa2=np.array([p.kappa2 for p in params], dtype=np.float64),
+        d1=np.array([p.d1 for p in params], dtype=np.float64).reshape(len(params), n),
+        alpha1=np.array([p.alpha1 for p in params], dtype=np.float64).reshape(len(params), n),
+        d2=np.array([p.d2 for p in params], dtype=np.float64).reshape(len(params), n),
+        alpha2=np.array([p.alpha2 for p in params], dtype=np.float64).reshape(len(params), n),
+    )
+
+
+def recursion_ab(d, alpha, kappa, dt):
+    """(a, b) of Eqs. relaxation_a / relaxation_b, elementwise, FP64."""
+    d = np.asarray(d, dtype=np.float64)
+    alpha = np.asarray(alpha, dtype=np.float64)
+    kappa = np.asarray(kappa, dtype=np.float64)
+    b = np.exp(-(d / kappa + alpha) * dt)
+    a = d / (kappa * (d + kappa * alpha)) * (b - 1.0)
+    return a, b
+
+
+def cfl_dt(cfl, dx, c, cls, table):
+    """dt = CFL dx / max over voxels of c/sqrt(kappa_1 kappa_2)."""
+    ceff = np.asarray(c, np.float64) / np.sqrt(table["kappa1"][cls] * table["kappa2"][cls])
+    return float(cfl * dx / np.max(ceff))
+
+
+def _inherit(a, width, axes):
+    """Replace the outer ``width`` layer of the listed axes by the nearest
+    interior value."""
+    a = np.asarray(a)
+    if width <= 0:
+        return a
+    idx = []
+    for ax, n in enumerate(a.shape):
+        if ax in axes:
+            lo, hi = min(width, n - 1), max(n - 1 - width, 0)
+            if lo > hi:
+                lo = hi = n // 2
+            idx.append(np.clip(np.arange(n), lo, hi))
+        else:
+            idx.append(np.arange(n))
+    return a[np.ix_(*idx)]
+
+
+def absorbing_depth(n, width, staggered):
+    """Depth s [cells] into the absorbing layer of points 0..n-1 along one axis
+    (staggered: the point sits at i + 1/2)."""
+    x = np.arange(n, dtype=np.float64) + (0.5 if staggered else 0.0)
+    left = (width - 0.5) - x
+    right = x - (n - width - 0.5)
+    return np.maximum(0.0, np.maximum(left, right))
+
+
+def absorbing_profile(s, l_t, l_b, d_max, f0):
+    s = np.asarray(s, dtype=np.float64)
+    if l_t > 0:
+        d = np.where(s <= l_t, 0.1 * d_max * (s / l_t) ** 2,
+                     d_max * (0.1 + 0.9 * ((s - l_t) / l_b) ** 2))
+    else:
+        d = d_max * (s / l_b) ** 2
+    d = np.where(s > 0.0, d, 0.0)
+    alpha = math.pi * f0 * (1.0 - s / (l_t + l_b))
+    return d, alpha
+
+
+class OracleMedium:
+    """Coefficient arrays of one medium (numpy C order; axis -1 is x).
+
+    Parameters
+    ----------
+    shape      : (ny, nx) or (nz, ny, nx)
+    c, rho     : maps [m/s], [kg/m^3]
+    cls        : integer class map into ``params`` (list of RelaxParams)
+    beta       : nonlinearity map or None
+    pml, transition : L_B and L_T in cells (0 = no absorbing layer)
+    periodic   : per numpy axis, for the pin tests (no absorbing layer on those axes)
+    dscale     : optional per-voxel factor on every d of the tissue mechanisms
+    """
+
+    def __init__(self, shape, dx, dt, c, rho, cls, params, beta=None, pml=0, transition=0,
+                 f0=3e6, R0=1e-5, periodic=None, dscale=None):
+        self.shape = tuple(shape)
+        self.ndim = len(shape)
+        self.dx, self.dt = float(dx), float(dt)
+        self.periodic = tuple(periodic) if periodic is not None else (False,) * self.ndim
+        width = pml + transition
+        self.width = width
+        self.pml, self.transition = pml, transition
+        # the absorbing layer lines every non-periodic axis
+        self.abs_axes = tuple(ax for ax in range(self.ndim) if not self.periodic[ax])
+        inh = lambda a, dt_: _inherit(np.asarray(a, dt_), width, self.abs_axes)  # noqa: E731
+        c = inh(c, np.float64)
+        rho = inh(rho, np.float64)
+        cls = inh(cls, np.int64)
+        beta = None if beta is None else inh(beta, np.float64)
+        self.c, self.rho, self.cls = c, rho, cls
+        tab = class_table(params)
+        self.table = tab
+        self.nmech = tab["d1"].shape[1]
+        K = rho * c * c
+        self.K = K
+        self.kdt = K * self.dt
+        self.b2dt = None if (beta is None or not np.any(beta)) else 2.0 * beta * self.dt
+        # face density per direction (numpy axis ax <-> direction d = ndim-1-ax)
+        self.dt_rho = []
+        for d in range(self.ndim):
+            ax = self.ndim - 1 - d
+            nxt = np.roll(rho, -1, axis=ax)
+            if not self.periodic[ax]:
+                last = [slice(None)] * self.ndim
+                last[ax] = -1
+                nxt[tuple(last)] = rho[tuple(last)]
+            self.dt_rho.append(self.dt / (0.5 * (rho + nxt)))
+        # tissue mechanisms, optional per-voxel scale of d (used by gradients w.r.t. alpha0)
+        k1 = tab["kappa1"][cls]
+        k2 = tab["kappa2"][cls]
+        self.ik1 = 1.0 / k1
+        self.ik2 = 1.0 / k2
+        self.a1, self.b1, self.a2, self.b2 = [], [], [], []
+        for nu in range(self.nmech):
+            sc = 1.0 if dscale is None else np.asarray(dscale, np.float64)
+            a, b = recursion_ab(tab["d1"][cls, nu] * sc, tab["alpha1"][cls, nu], k1, self.dt)
+            self.a1.append(a)
+            self.b1.append(b)
+            a, b = recursion_ab(tab["d2"][cls, nu] * sc, tab["alpha2"][cls, nu], k2, self.dt)
+            self.a2.append(a)
+            self.b2.append(b)
+        # absorbing mechanism per direction
+        self.a1p = [None] * self.ndim
+        self.b1p = [None] * self.ndim
+        self.a2p = [None] * self.ndim
+        self.b2p = [None] * self.ndim
+        if width > 0:
+            cmax = float(np.max(c))
+            d_max = -3.0 * cmax * math.log(R0) / (2.0 * pml * self.dx)
+            for d in range(self.ndim):
+                ax = self.ndim - 1 - d
+                if ax not in self.abs_axes:
+                    continue
+                n = self.shape[ax]
+                bshape = [1] * self.ndim
+                bshape[ax] = n
+                for stag, k, dst_a, dst_b in ((True, k1, self.a1p, self.b1p),
+                                              (False, k2, self.a2p, self.b2p)):
+                    s = absorbing_depth(n, width, stag)
+                    dd, al = absorbing_profile(s, transition, pml, d_max, f0)
+                    dd = np.broadcast_to(dd.reshape(bshape), self.shape)
+                    al = np.broadcast_to(al.reshape(bshape), self.shape)
+                    a, b = recursion_ab(dd, al, k, self.dt)
+                    dst_a[d] = np.ascontiguousarray(a)
+                    dst_b[d] = np.ascontiguousarray(b)
+
+    def source_gain(self, idx):
+        """Volume-source gain K dt / dx^D at linear indices ``idx``."""
+        return self.kdt.ravel()[idx] / self.dx ** self.ndim
