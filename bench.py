@@ -1,0 +1,420 @@
+#!/usr/bin/env python
+"""Throughput bench of the heterogeneous power-law attenuation FDTD.
+
+Workload (default): 3D seeded Voronoi tissue map 512^3, 8 classes, 2 % c/rho
+jitter, N = 4 relaxation mechanisms per class calibrated on the host, 20-cell
+absorbing layer, 3 MHz focused square aperture (65 536 source cells) and a
+strided receiver grid; FP32 arithmetic and storage.
+
+One bench step = one time step of the whole grid (velocity sweep, pressure
+sweep, sources, receivers).  Metric: voxel-updates per second (Gvox/s, one
+voxel advanced by one full time step).  The working set (~15 GB) is far
+larger than L2, so no flush is needed between steps.
+
+Prints ONE JSON line on rank 0.  ``--impl reference`` times the FP64 CPU
+oracle (the reference arm of this build) on a crop of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes as C
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"])
+    ap.add_argument("--size", type=int, default=512, help="cube side (512 = the 3D Voronoi workload)")
+    ap.add_argument("--e2e-steps", type=int, default=0, help="streaming end-to-end steps (0: = --steps)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas: one independent simulation per GPU)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# workload
+
+
+def workload(args, n_steps):
+    from synthetic import config_c3
+    n = args.size
+    if n == 512:
+        spec = config_c3(n_steps=n_steps)
+    else:
+        lo = (512 - n) // 2
+        box = ((0, n), (lo, lo + n), (lo, lo + n))
+        spec = config_c3(n_steps=n_steps, box=box)
+    return spec
+
+
+def fit_classes(spec):
+    """Host FP64 calibration of every class (paper settings), one thread per class."""
+    import paper_2606_11103_gb300 as fw
+    out = [None] * len(spec.classes["alpha0"])
+    reps = [None] * len(out)
+
+    def job(i):
+        out[i], reps[i] = fw.fit_relaxation(float(spec.classes["alpha0"][i]), float(spec.classes["y"][i]), 4,
+                                            c0=float(spec.classes["c"][i]))
+
+    th = [threading.Thread(target=job, args=(i,)) for i in range(len(out))]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    return out, reps
+
+
+def alg_bytes(ndim, nmech, storage, nonlinear, wabs, shape):
+    """Algorithmic bytes per voxel of each sweep and of the minimal single-pass
+    step (every field read once and written once, maps read once)."""
+    es = 4
+    eps = {"f32": 4, "bf16": 2, "f16": 2}[storage]
+    D = ndim
+    n_axes = list(shape)
+
+    def frac(half):
+        f = []
+        for n in n_axes:
+            act = (2 * wabs - 1) if half else 2 * wabs
+            f.append(min(act, n) / n if wabs > 0 else 0.0)
+        return f
+
+    pml_v = sum(frac(True)) * 2 * es
+    pml_p = sum(frac(False)) * 2 * es
+    vel = es + 2 * D * es + 2 * D * nmech * eps + es + 2 + pml_v
+    pres = D * es + 2 * es + 2 * nmech * eps + es + (es if nonlinear else 0) + 2 + pml_p
+    single = 2 * es + 2 * D * es + 2 * D * nmech * eps + 2 * nmech * eps + es + es + 2 + \
+        (es if nonlinear else 0) + pml_v + pml_p
+    return vel, pres, single
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ("fw_kernels.cuh", "fw_launch.cuh"):
+        with open(os.path.join(ROOT, "paper_2606_11103_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(vox, key="velocity"):
+    """DRAM bytes per launch of the sweep from the committed ncu summary, or
+    None when the kernel source changed since the counters were taken."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("kernel_sha") != kernel_source_sha() or key not in d:
+        return None
+    return d[key]["bytes_per_voxel"] * vox
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# oracle timing (cpu_baseline leg and the reference arm)
+
+
+def oracle_sim(crop=128, n_steps=8):
+    from oracle import fit
+    from oracle.medium import OracleMedium
+    from oracle.stepper import OracleSim
+    from synthetic import config_c3
+    lo = (512 - crop) // 2
+    spec = config_c3(n_steps=n_steps, box=((0, crop), (lo, lo + crop), (lo, lo + crop)))
+    params = []
+    for a, y in zip(spec.classes["alpha0"], spec.classes["y"]):
+        p, _ = fit.fit_relaxation(float(a), float(y), 4, maxiter=200, w_list=(0.5,))
+        params.append(p)
+    med = OracleMedium(spec.shape, spec.dx, spec.dt, spec.maps["c"], spec.maps["rho"],
+                       spec.maps["class_idx"].astype(np.int64), params, pml=spec.pml, f0=spec.f0)
+    sim = OracleSim(med)
+    sim.set_sources(spec.src_mask, spec.src_waves.astype(np.float64), spec.src_wave_of)
+    sim.set_receivers(spec.rcv_mask, n_steps)
+    return sim, int(np.prod(spec.shape))
+
+
+def time_oracle(budget_s, crop=128):
+    sim, vox = oracle_sim(crop, n_steps=4096)
+    sim.run(1)                      # thread start-up
+    t0 = time.perf_counter()
+    sim.run(2)
+    one = (time.perf_counter() - t0) / 2
+    k = max(1, min(2000, int(budget_s / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    sim.run(k)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": vox * k / dt / 1e9, "unit": "Gvoxel-updates/s", "cores": cores, "kind": "oracle",
+            "sample": "FP64 C oracle, %d^3 crop of the 512^3 Voronoi workload (N=4, 20-cell PML), %d time steps, "
+                      "%.1f s" % (crop, k, dt)}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    crop = 96
+    sim, vox = oracle_sim(crop, n_steps=args.warmup + args.steps + 1)
+    sim.run(args.warmup)
+    t0 = time.perf_counter()
+    sim.run(args.steps)
+    dt = time.perf_counter() - t0
+    v = vox * args.steps / dt / 1e9
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    out = {"impl": "reference", "metric": "voxel-updates/s (3D FP32)", "value": v, "unit": "Gvoxel-updates/s",
+           "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": "3D Voronoi 512^3 N=4, FP64 CPU oracle on a %d^3 crop" % crop},
+           "cpu_baseline": {"value": v, "unit": "Gvoxel-updates/s", "cores": cores, "kind": "oracle",
+                            "sample": "%d^3 crop, %d steps" % (crop, args.steps)},
+           "e2e": {"value": v, "unit": "Gvoxel-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", rank=rank, world_size=ws)
+    torch.cuda.set_device(local)
+    import paper_2606_11103_gb300 as fw
+    from paper_2606_11103_gb300 import build as fwbuild
+    if rank == 0:
+        fwbuild.build()
+    barrier(ws)
+    L = fw.lib()
+
+    K, W = args.steps, args.warmup
+    K2 = args.e2e_steps or K
+    n_total = W + K + K2 + 2
+    t0 = time.perf_counter()
+    spec = workload(args, n_total)
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    classes, reps = fit_classes(spec)
+    t_fit = time.perf_counter() - t0
+    log("workload %s generated in %.1fs, %d classes fitted in %.1fs (max NRMSE %.3f)" %
+        (spec.name, t_gen, len(classes), t_fit, max(r.nrmse for r in reps)))
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    m = fw.Medium.from_classes(spec.shape, spec.dx, spec.maps["c"], spec.maps["rho"], spec.maps["class_idx"],
+                               classes, dt=spec.dt, pml=spec.pml, f0=spec.f0, storage=args.storage)
+    m.set_sources(spec.src_mask, spec.src_waves, spec.src_wave_of)
+    m.set_receivers(spec.rcv_mask, n_total)
+    t_create = time.perf_counter() - t0
+    info = m.info()
+    vox = int(np.prod(spec.shape))
+    log("medium: %.2f GB on device, created in %.1fs, dt %.3e" % (info["device_bytes"] / 1e9, t_create, info["dt"]))
+
+    # warm-up (graph path and the timed path)
+    m.run(W)
+    torch.cuda.synchronize()
+
+    # ---- timed region: per-sweep CUDA events on the launch stream ----
+    ms_v, ms_p, ms_io = C.c_double(), C.c_double(), C.c_double()
+    nl = C.c_int()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier(ws)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        fw.check(L.fw_step_timed(m.h, K, C.c_void_p(stream.cuda_stream), C.byref(ms_v), C.byref(ms_p),
+                                 C.byref(ms_io), C.byref(nl)), "fw_step_timed")
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier(ws)
+    ms = allmax(ev0.elapsed_time(ev1), ws)
+    rc, pmax = m.status()
+    if rc != 0:
+        raise RuntimeError("unstable run: %s" % fw.FwError(rc))
+    value = ws * vox * K / (ms / 1e3) / 1e9
+
+    # ---- end to end through the C ABI: per step, the step's waveform samples
+    # go host->device from pinned memory and the step's receiver samples come
+    # back device->host into pinned memory ----
+    nw, nr = spec.src_waves.shape[0], int(info["n_rcv"])
+    h_w = torch.from_numpy(np.ascontiguousarray(spec.src_waves.T)).pin_memory()   # [steps][n_wave]
+    h_r = torch.empty((K2, nr), dtype=torch.float32).pin_memory()
+    it0 = info["step"]
+    sp = C.c_void_p(stream.cuda_stream)
+    barrier(ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for j in range(K2):
+        it = it0 + j
+        fw.check(L.fw_set_waveform_samples(m.h, it, 1, C.c_void_p(h_w[it].data_ptr()), sp), "waveforms")
+        fw.check(L.fw_run(m.h, 1, sp), "fw_run")
+        fw.check(L.fw_read_receivers_range(m.h, it, 1, C.c_void_p(h_r[j].data_ptr()), sp), "receivers")
+    torch.cuda.synchronize()
+    t_e2e = allmax(time.perf_counter() - t0, ws)
+    e2e = ws * vox * K2 / t_e2e / 1e9
+    assert np.isfinite(h_r.numpy()).all()
+
+    # ---- roofline of the dominant kernel (velocity sweep) ----
+    b_vel, b_pres, b_single = alg_bytes(3, 4, args.storage, False, spec.pml, spec.shape)
+    peak, peak_kind = measured_peaks()
+    t_vel = ms_v.value / K / 1e3
+    t_pres = ms_p.value / K / 1e3
+    ach = b_vel * vox / t_vel / 1e9
+    traffic = profiled_traffic(vox, "velocity")
+    roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(ach / peak, 4), "traffic": traffic, "kernel": "k_velocity (velocity sweep)",
+            "peak_source": "%s hbm_gbs" % peak_kind}
+    step_info = {
+        "velocity_ms": round(t_vel * 1e3, 4), "pressure_ms": round(t_pres * 1e3, 4),
+        "io_ms": round(ms_io.value / K, 4),
+        "pressure_gbs": round(b_pres * vox / t_pres / 1e9, 1),
+        "alg_bytes_per_voxel": {"velocity": round(b_vel, 2), "pressure": round(b_pres, 2),
+                                "single_pass_min": round(b_single, 2)},
+        "step_gbs_vs_single_pass_min": round(b_single * vox * K / (ms / 1e3) / 1e9, 1),
+        "frac_step_vs_single_pass_min": round(b_single * vox * K / (ms / 1e3) / 1e9 / peak, 4),
+    }
+    out = {
+        "metric": "voxel-updates/s (3D FP32)", "value": round(value, 3), "unit": "Gvoxel-updates/s",
+        "n_gpus": ws, "steps": K, "warmup": W, "ms_per_step": round(ms / K, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.storage == "f32" else "f32/%s-psi" % args.storage,
+        "data": "synthetic",
+        "config": {"workload": "3D seeded Voronoi %d^3, 8 classes, N=4, 20-cell PML, focused 3 MHz aperture"
+                               % args.size, "voxels": vox, "storage": args.storage,
+                   "l2": "working set %.1f GB >> 129 MB L2, no flush needed" % (info["device_bytes"] / 1e9),
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "e2e": {"value": round(e2e, 3), "unit": "Gvoxel-updates/s", "h2d_bytes_per_step": nw * 4,
+                "d2h_bytes_per_step": nr * 4, "steps": K2},
+        "gpu_launches": int(nl.value),
+        "roofline": roof,
+        "step": step_info,
+        "clocks": clk.summary(),
+        "max_abs_p": pmax,
+    }
+    m.close()
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = time_oracle(args.cpu_seconds)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,284 @@
+/*
+ * fullwave_gb.h -- C ABI of the GB300 (sm_103a) heterogeneous power-law
+ * attenuation FDTD library.
+ *
+ * Method: Sode & Pinton, "Spatially heterogeneous power-law attenuation with
+ * multiple relaxation mechanisms for ultrasound modeling".  The library
+ * calibrates N Debye relaxation mechanisms per tissue class on the host
+ * (Sec. 3.1-3.2), builds a device-resident medium (Sec. 2.1, Sec. 4.6), and
+ * advances the stretched pressure-velocity system on the GPU (Sec. 2.1,
+ * Sec. 3.3).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Return value: FW_OK (0) or a negative FW_ERR_* code; no call throws,
+ *   aborts or exits.  fw_strerror() names a code.  Errors raised by work
+ *   already queued on a stream (non-finite pressure) are sticky on the
+ *   medium and reported by fw_status().
+ * - Units are SI (m, s, kg/m^3, Pa, m/s); alpha0 is in dB/(MHz^y cm).
+ * - Maps are C-order: 3D [nz][ny][nx], 2D [ny][nx]; x is the fastest axis
+ *   and the slowest axis is depth.  In 2D the physical directions are x and
+ *   the depth axis y.
+ * - Pointer arguments documented as "host or device" may point to pageable
+ *   or pinned host memory or to device memory of the current device; the
+ *   library copies what it needs and never keeps the caller's pointer.
+ *   The caller owns every buffer it passes in.
+ * - "stream" arguments are cudaStream_t values passed as void* (NULL = the
+ *   legacy default stream).  Calls that take a stream are asynchronous with
+ *   respect to the host unless stated otherwise.
+ * - Device memory of a medium comes from the allocator installed with
+ *   fw_set_allocator() (cudaMalloc by default) and is released by
+ *   fw_destroy_medium().
+ */
+#ifndef FULLWAVE_GB_H
+#define FULLWAVE_GB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FW_MAX_MECH 4
+#define FW_MAX_W 8
+
+/* error codes */
+#define FW_OK 0
+#define FW_ERR_ARG (-1)         /* invalid argument (sizes, ranges, CFL)      */
+#define FW_ERR_CUDA (-2)        /* a CUDA runtime call failed                 */
+#define FW_ERR_NOMEM (-3)       /* device or host allocation failed           */
+#define FW_ERR_UNSTABLE (-4)    /* non-finite pressure seen by the monitor    */
+#define FW_ERR_STATE (-5)       /* call not valid in the medium's state       */
+#define FW_ERR_UNSUPPORTED (-6) /* combination not compiled into the library  */
+
+/* storage of the memory variables psi (fields p, v are FP32 unless F64) */
+#define FW_STORE_F32 0   /* FP32 everything                                   */
+#define FW_STORE_BF16 1  /* psi in bfloat16, FP32 arithmetic                  */
+#define FW_STORE_F16 2   /* psi in binary16 (scaled units), FP32 arithmetic   */
+#define FW_STORE_F64 3   /* FP64 everything: verification build of the kernels */
+
+/* fields for fw_read_field */
+#define FW_FIELD_P 0     /* pressure p at integer points                        */
+#define FW_FIELD_V 1     /* velocity v_d, idx = d, at i + 1/2 along d           */
+#define FW_FIELD_PSI1 2  /* gradient-side memory variable, idx = nu*ndim + d    */
+#define FW_FIELD_PSI2 3  /* divergence-side memory variable summed over d, idx = nu */
+#define FW_FIELD_PSI1P 4 /* absorbing-layer mechanism, gradient side, idx = d   */
+#define FW_FIELD_PSI2P 5 /* absorbing-layer mechanism, divergence side, idx = d */
+
+/* Grid and time step (Sec. 3.3).  The absorbing layer (transition L_T plus
+ * absorbing L_B cells) lines every side inside the nx*ny*nz grid; its maps
+ * are replaced by the nearest interior values (adaptive PML, Sec. 4.6). */
+typedef struct fw_grid {
+    int ndim;          /* 2 or 3                                               */
+    int nx, ny, nz;    /* points; 2D uses nz = 1                               */
+    double dx;         /* grid step [m], > 0                                   */
+    double dt;         /* time step [s]; <= 0 selects dt from cfl              */
+    double cfl;        /* dt = cfl*dx/max(c/sqrt(kappa1 kappa2)) when dt <= 0  */
+    int pml;           /* L_B cells (0: no absorbing layer)                    */
+    int transition;    /* L_T cells                                            */
+    double f0;         /* centre frequency [Hz] of the absorbing profile       */
+    double pml_r0;     /* design reflection of the profile, <= 0 means 1e-5    */
+} fw_grid;
+
+/* Relaxation parameters of one class (Sec. 2.1): kappa_x1, kappa_x2 and for
+ * each mechanism nu d^nu and alpha^nu of both stretches.  2 + 4N values. */
+typedef struct fw_relax_params {
+    int n_mech;                    /* N, 1..FW_MAX_MECH                        */
+    double kappa1, kappa2;
+    double d1[FW_MAX_MECH], alpha1[FW_MAX_MECH];
+    double d2[FW_MAX_MECH], alpha2[FW_MAX_MECH];
+} fw_relax_params;
+
+/* Options of the calibration (Sec. 3.2); fw_fit_default_opts fills the
+ * paper's values: 1-20 MHz, 200 log-spaced samples, w in {.1,.3,.5,.7,.9},
+ * 5e4 iterations, tolerance 1e-25, reference frequency 1 MHz, c0 1540 m/s. */
+typedef struct fw_fit_opts {
+    double f_min, f_max;   /* band [Hz]                                        */
+    int n_freq;            /* log-spaced samples                               */
+    int n_w;               /* number of weights in w[]                         */
+    double w[FW_MAX_W];    /* real/imaginary balance weights                   */
+    int maxiter;           /* Nelder-Mead iterations                           */
+    double xatol, fatol;   /* simplex spread tolerances                        */
+    double f_ref;          /* omega_0 / 2 pi of the Kramers-Kronig relation    */
+    double c0;             /* phase velocity at f_ref [m/s]                    */
+    int n_threads;         /* host threads for the weight sweep, <= 0: all     */
+} fw_fit_opts;
+
+typedef struct fw_fit_report {
+    double J;          /* objective at the selected weight                     */
+    double w;          /* selected weight                                      */
+    double nrmse;      /* attenuation NRMSE of the model vs alpha0 f^y         */
+    double disp_rmse;  /* phase-velocity RMSE vs Kramers-Kronig [m/s]          */
+    int failed;        /* NRMSE > 10 % or dispersion error > 5 m/s (Sec. 3.2)  */
+    int n_iter, n_eval;
+} fw_fit_report;
+
+typedef struct fw_medium fw_medium;
+
+typedef struct fw_medium_info {
+    int ndim, nx, ny, nz, n_mech, storage, n_classes, nonlinear;
+    double dx, dt, c_max, ceff_max;
+    size_t device_bytes;
+    long long step;    /* completed time steps                               */
+    int n_src, n_rcv, n_rec;
+} fw_medium_info;
+
+/* ---- calibration (host, FP64) ------------------------------------------- */
+
+/* Fill *opts with the paper's defaults (see fw_fit_opts). */
+void fw_fit_default_opts(fw_fit_opts *opts);
+
+/* Calibrate N mechanisms to alpha(f) = alpha0 f^y and its Kramers-Kronig
+ * dispersion (Sec. 3.1-3.2, Table 2): adaptive Nelder-Mead on the
+ * normalised complex-wavenumber objective for every weight of opts->w, the
+ * weight with the lowest attenuation NRMSE kept (dispersion error breaks
+ * ties).  alpha0 = 0 returns the lossless set (d = 0, kappa = 1) without
+ * fitting.  opts may be NULL (defaults).  Errors: FW_ERR_ARG for n_mech
+ * outside 1..4, alpha0 < 0, y outside [0.1, 3], or bad opts.  A poor fit is
+ * not an error: rep->failed is set.  rep may be NULL.  Blocking; thread-safe. */
+int fw_fit_relaxation(double alpha0, double y, int n_mech, const fw_fit_opts *opts,
+                      fw_relax_params *out, fw_fit_report *rep);
+
+/* The objective J(theta) of Sec. 3.2 for one weight w, theta in the Table 2
+ * layout [kappa1, kappa2, then per mechanism log10 d1, log10 d2, log10 a1,
+ * log10 a2] (2 + 4N doubles).  For inspection and tests. */
+int fw_fit_objective(double alpha0, double y, double w, const fw_fit_opts *opts,
+                     const double *theta, int n_mech, double *J);
+
+/* Model complex wavenumber of Eq. dispersion_relations for a parameter set
+ * and medium speed c at n frequencies f_hz: writes Re k and Im k (attenuation
+ * is -Im k).  Host arrays of n doubles. */
+int fw_model_wavenumber(const fw_relax_params *p, double c, const double *f_hz, int n,
+                        double *k_re, double *k_im);
+
+/* Adaptive bounded Nelder-Mead used by the calibration (Gao & Han
+ * coefficients, bounds by clipping), exposed for reuse: minimises f over n
+ * variables starting from x (overwritten with the minimiser).  lo/hi may be
+ * NULL (unbounded).  fmin, n_iter, n_eval may be NULL. */
+int fw_nelder_mead(int n, double *x, const double *lo, const double *hi,
+                   double (*f)(const double *x, void *ctx), void *ctx,
+                   int maxiter, double xatol, double fatol,
+                   double *fmin, int *n_iter, int *n_eval);
+
+/* ---- media ------------------------------------------------------------- */
+
+/* Install the device allocator used for every later medium (NULL, NULL
+ * restores cudaMalloc/cudaFree).  alloc returns NULL on failure. */
+void fw_set_allocator(void *(*alloc)(size_t bytes, void *ctx),
+                      void (*release)(void *ptr, void *ctx), void *ctx);
+
+/* Device bytes a medium of this grid needs (state, maps, tables; not the
+ * source/receiver buffers).  For admission control. */
+int fw_medium_bytes(const fw_grid *g, int n_mech, int storage, int nonlinear, size_t *bytes);
+
+/* Build a medium from per-voxel maps (Sec. 2.1, Sec. 4.6): every distinct
+ * (alpha0, y) pair becomes a class calibrated with fw_fit_relaxation (on
+ * host threads, one job per class and weight); the class's reference speed
+ * c0 is opts->c0 when opts is given with c0 > 0, else the mean c of the
+ * class's voxels.  c, rho, alpha0, y: host or device float arrays of
+ * nx*ny*nz values; beta may be NULL (linear).  The rest is as in
+ * fw_create_medium_classes.
+ * Errors: FW_ERR_ARG (non-positive c or rho, y outside [0.1, 3] where
+ * alpha0 > 0, more than 65535 classes, CFL above the stability limit),
+ * FW_ERR_NOMEM, FW_ERR_CUDA.  Blocking (returns when the medium is ready). */
+int fw_create_medium(const fw_grid *g, const float *c, const float *rho, const float *beta,
+                     const float *alpha0, const float *y, int n_mech, int storage,
+                     const fw_fit_opts *opts, void *stream, fw_medium **out);
+
+/* Build a medium from a class map and a class table: class_idx (uint16,
+ * host or device, nx*ny*nz) indexes classes[0..n_classes-1], all with the
+ * same n_mech.  Per-voxel c, rho, beta as above.  A velocity point v_d[i]
+ * (at i+1/2 along d) uses the class of cell i.  The stability limit on
+ * c_eff*dt/dx is 1/(sqrt(D) sum|c_m|) = 0.5497 (2D), 0.4488 (3D).  Blocking. */
+int fw_create_medium_classes(const fw_grid *g, const float *c, const float *rho,
+                             const float *beta, const uint16_t *class_idx,
+                             const fw_relax_params *classes, int n_classes, int storage,
+                             void *stream, fw_medium **out);
+
+/* Optional per-voxel factor s(x) on every d of the tissue mechanisms
+ * (d^nu(x) = s(x) d^nu_class): the map used to take gradients with respect
+ * to alpha0(x).  Host or device floats; NULL restores s = 1.  Blocking. */
+int fw_set_dscale(fw_medium *m, const float *s, void *stream);
+
+/* Sources (additive volume sources on p): mask (host, uint8, nx*ny*nz)
+ * selects cells in C order; waveforms (host, n_wave x n_steps floats, volume
+ * rate [m^D/s]); wave_of_src (host, one int per source in mask order) picks
+ * a waveform row, or NULL: one shared row (n_wave = 1) or one row per source
+ * (n_wave = n_src).  Time step `it` adds dt*K/dx^D * waveform[it] after the
+ * pressure update (nothing once it >= n_steps).  Replaces earlier sources. */
+int fw_set_sources(fw_medium *m, const uint8_t *mask, const float *waveforms, int n_wave,
+                   int n_steps, const int32_t *wave_of_src);
+
+/* Receivers: mask (host, uint8) selects cells in C order; time step `it`
+ * records p after the source into column it/decim when it % decim == 0, for
+ * it < n_steps.  Traces are [n_rcv][ceil(n_steps/decim)] and are zeroed. */
+int fw_set_receivers(fw_medium *m, const uint8_t *mask, int decim, int n_steps);
+
+/* Advance n_steps time steps on stream with plain kernel launches. */
+int fw_step(fw_medium *m, int n_steps, void *stream);
+
+/* Advance n_steps time steps on stream through cached CUDA graphs of fixed
+ * step chunks (the fast path; same results as fw_step). */
+int fw_run(fw_medium *m, int n_steps, void *stream);
+
+/* fw_step with a CUDA event around each sweep: advances n_steps on stream
+ * (plain launches), waits for them, and returns the summed device time [ms]
+ * of the velocity sweeps, the pressure sweeps and the source/receiver
+ * kernels, and the number of kernels launched.  Output pointers may be
+ * NULL.  For measurement; results equal fw_step's. */
+int fw_step_timed(fw_medium *m, int n_steps, void *stream, double *ms_velocity, double *ms_pressure,
+                  double *ms_io, int *n_launches);
+
+/* Replace waveform samples [it0, it0+n) of every waveform row from samples
+ * (n_wave x n floats, host or device; pinned host memory keeps the copy
+ * asynchronous).  Ordered on stream.  FP32 and 16-bit media only
+ * (FW_ERR_UNSUPPORTED for FW_STORE_F64).  For streaming inputs step by step. */
+int fw_set_waveform_samples(fw_medium *m, int it0, int n, const float *samples, void *stream);
+
+/* Copy trace columns [col0, col0+ncol) of every receiver to dst
+ * (n_rcv x ncol, host or device, in the medium's field type: float, double
+ * for FW_STORE_F64).  Ordered on stream; asynchronous for pinned or device
+ * dst.  For streaming results step by step. */
+int fw_read_receivers_range(fw_medium *m, int col0, int ncol, void *dst, void *stream);
+
+/* Copy a field to dst (host or device), unpadded C order, as float
+ * (as_f64 = 0) or double (as_f64 = 1).  Ordered on stream; blocking. */
+int fw_read_field(fw_medium *m, int which, int idx, void *dst, int as_f64, void *stream);
+
+/* Write a field from src (host or device, same layout/type rules).  For
+ * initial conditions and tests.  Blocking. */
+int fw_write_field(fw_medium *m, int which, int idx, const void *src, int as_f64, void *stream);
+
+/* Copy the receiver traces [n_rcv][n_rec] to dst (host or device) as float
+ * or double.  Blocking. */
+int fw_read_receivers(fw_medium *m, void *dst, int as_f64, void *stream);
+
+/* Full state (every field, memory variable, step counter) as an opaque
+ * byte image for checkpoint/resume: fw_state_bytes gives its size,
+ * fw_save_state copies it to dst, fw_load_state restores it (host or
+ * device buffers).  Blocking.  Resuming is bit-exact. */
+int fw_state_bytes(fw_medium *m, size_t *bytes);
+int fw_save_state(fw_medium *m, void *dst, void *stream);
+int fw_load_state(fw_medium *m, const void *src, void *stream);
+
+/* Stability monitor (non-finite pressure, Sec. 4.6): synchronises the
+ * medium's last stream and returns FW_OK or FW_ERR_UNSTABLE (sticky);
+ * max_abs_p (may be NULL) receives max |p| seen since creation. */
+int fw_status(fw_medium *m, float *max_abs_p);
+
+int fw_medium_get_info(fw_medium *m, fw_medium_info *info);
+
+/* Release the medium and all its device memory (NULL is ignored). */
+void fw_destroy_medium(fw_medium *m);
+
+const char *fw_strerror(int code);
+
+/* Library version: major*10000 + minor*100 + patch. */
+int fw_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FULLWAVE_GB_H */

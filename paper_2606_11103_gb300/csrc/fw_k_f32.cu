@@ -1,0 +1,8 @@
+// FP32 state and FP32 memory variables.
+#include "fw_launch.cuh"
+
+namespace fwgb {
+cudaError_t sweeps_f32(const fw_medium *m, cudaStream_t s, int which) { return launch_sweeps<float, float, float>(m, s, which); }
+cudaError_t io_f32(const fw_medium *m, int j, cudaStream_t s) { return launch_io<float, float>(m, j, s); }
+__global__ void k_advance(int *d_it, int n) { *d_it += n; }
+}  // namespace fwgb

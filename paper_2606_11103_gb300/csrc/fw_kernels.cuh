@@ -1,0 +1,585 @@
+// Fused staggered-grid FDTD kernels for sm_103a (Sec. 2.1, Sec. 3.3).
+//
+// One time step is two z-marching sweeps over the grid:
+//   velocity sweep : g_d = D+_d p (8th order), memory variables of the
+//                    gradient side, absorbing-layer mechanism, v_d update;
+//   pressure sweep : q_d = D-_d v_d, memory variables of the divergence side
+//                    (summed over directions, exact because their
+//                    coefficients do not depend on d), absorbing-layer
+//                    mechanism per direction, p update (with the optional
+//                    nonlinear factor), stability monitor.
+// Every field is read once and written once per sweep from HBM: each thread
+// owns 4 consecutive x points of one (x, y) column and walks the depth axis;
+// the depth-direction taps come from a register queue of 8 planes, the x and
+// y taps from a double-buffered shared-memory plane tile with halos, and all
+// global traffic is 128-bit (FP32) and coalesced.
+//
+// Memory-variable update (Eq. relaxation_psi, midpoint time index): with the
+// derivative g of the current half step, psi_new = b psi_old + a g, and the
+// stretched derivative is g/kappa + sum (psi_old + psi_new)/2
+//   = g * ceff + sum hb * psi_old,   ceff = 1/kappa + sum a/2,  hb = (1+b)/2,
+// with a, b of Eqs. relaxation_a/b from the class table.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fw_internal.h"
+
+namespace fwgb {
+
+constexpr int kMaxMech = FW_MAX_MECH;
+
+// ---------------------------------------------------------------------------
+// 4-element vector access in the storage type S, arithmetic in R
+
+template <typename S> struct Io;
+
+template <> struct Io<float> {
+    template <typename R> static __device__ __forceinline__ void ld(const float *p, R (&v)[4])
+    {
+        float4 t = __ldcs(reinterpret_cast<const float4 *>(p));
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    }
+    template <typename R> static __device__ __forceinline__ void ldg(const float *p, R (&v)[4])
+    {
+        float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    }
+    template <typename R> static __device__ __forceinline__ void st(float *p, const R (&v)[4])
+    {
+        __stcs(reinterpret_cast<float4 *>(p), make_float4(float(v[0]), float(v[1]), float(v[2]), float(v[3])));
+    }
+    static __device__ __forceinline__ float ld1(const float *p) { return *p; }
+    static __device__ __forceinline__ void st1(float *p, float v) { *p = v; }
+};
+
+template <> struct Io<double> {
+    template <typename R> static __device__ __forceinline__ void ld(const double *p, R (&v)[4])
+    {
+        double2 a = __ldcs(reinterpret_cast<const double2 *>(p));
+        double2 b = __ldcs(reinterpret_cast<const double2 *>(p) + 1);
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+    template <typename R> static __device__ __forceinline__ void ldg(const double *p, R (&v)[4])
+    {
+        double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+        double2 b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+    template <typename R> static __device__ __forceinline__ void st(double *p, const R (&v)[4])
+    {
+        __stcs(reinterpret_cast<double2 *>(p), make_double2(v[0], v[1]));
+        __stcs(reinterpret_cast<double2 *>(p) + 1, make_double2(v[2], v[3]));
+    }
+    static __device__ __forceinline__ double ld1(const double *p) { return *p; }
+    static __device__ __forceinline__ void st1(double *p, double v) { *p = v; }
+};
+
+template <> struct Io<__nv_bfloat16> {
+    template <typename R> static __device__ __forceinline__ void ld(const __nv_bfloat16 *p, R (&v)[4])
+    {
+        uint2 t = __ldcs(reinterpret_cast<const uint2 *>(p));
+        float2 a = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&t.x));
+        float2 b = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&t.y));
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+    template <typename R> static __device__ __forceinline__ void st(__nv_bfloat16 *p, const R (&v)[4])
+    {
+        __nv_bfloat162 a = __floats2bfloat162_rn(float(v[0]), float(v[1]));
+        __nv_bfloat162 b = __floats2bfloat162_rn(float(v[2]), float(v[3]));
+        uint2 t;
+        t.x = *reinterpret_cast<unsigned int *>(&a);
+        t.y = *reinterpret_cast<unsigned int *>(&b);
+        __stcs(reinterpret_cast<uint2 *>(p), t);
+    }
+};
+
+template <> struct Io<__half> {
+    template <typename R> static __device__ __forceinline__ void ld(const __half *p, R (&v)[4])
+    {
+        uint2 t = __ldcs(reinterpret_cast<const uint2 *>(p));
+        float2 a = __half22float2(*reinterpret_cast<__half2 *>(&t.x));
+        float2 b = __half22float2(*reinterpret_cast<__half2 *>(&t.y));
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+    template <typename R> static __device__ __forceinline__ void st(__half *p, const R (&v)[4])
+    {
+        __half2 a = __floats2half2_rn(float(v[0]), float(v[1]));
+        __half2 b = __floats2half2_rn(float(v[2]), float(v[3]));
+        uint2 t;
+        t.x = *reinterpret_cast<unsigned int *>(&a);
+        t.y = *reinterpret_cast<unsigned int *>(&b);
+        __stcs(reinterpret_cast<uint2 *>(p), t);
+    }
+};
+
+template <typename R> __device__ __forceinline__ void lut4(const R *lut, int c, int off, R (&v)[4]);
+template <> __device__ __forceinline__ void lut4<float>(const float *lut, int c, int off, float (&v)[4])
+{
+    float4 t = __ldg(reinterpret_cast<const float4 *>(lut + (size_t)c * kLutStride + off));
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+template <> __device__ __forceinline__ void lut4<double>(const double *lut, int c, int off, double (&v)[4])
+{
+    const double2 *q = reinterpret_cast<const double2 *>(lut + (size_t)c * kLutStride + off);
+    double2 a = __ldg(q), b = __ldg(q + 1);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
+__device__ __forceinline__ float fw_exp(float x) { return expf(x); }
+__device__ __forceinline__ double fw_exp(double x) { return exp(x); }
+
+// Absorbing-layer mechanism coefficients (Eqs. relaxation_a/b with the
+// profile d, alpha at this point and the point's tissue kappa).
+template <typename R>
+__device__ __forceinline__ void pml_ab(R d, R al, R kappa, R dt, R &a, R &b)
+{
+    b = fw_exp(-(d / kappa + al) * dt);
+    a = d / (kappa * (d + kappa * al)) * (b - R(1));
+}
+
+// ---------------------------------------------------------------------------
+// launch parameters
+
+template <typename R> struct Geo {
+    int nx, ny, nz;      // kernel axes (ny = 1 in 2D)
+    int px;              // row pitch (elements), multiple of 32
+    long long plane;     // px * ny
+    int zseg;            // depth planes per CTA
+    int wabs;            // absorbing width in cells (0: none)
+    R c1, c2, c3, c4;    // stencil weights / dx
+    R dt;
+};
+
+template <typename R, typename SS, typename SP> struct VelArgs {
+    Geo<R> g;
+    const SS *p;
+    SS *v[3];
+    SP *psi[kMaxMech][3];
+    SS *psip[3];                 // absorbing mechanism memory per axis, or null
+    const SS *rho;
+    const uint16_t *cls;
+    const R *lut;
+    const R *pd[3], *pa[3];      // absorbing profile at half points per axis
+};
+
+template <typename R, typename SS, typename SP> struct PresArgs {
+    Geo<R> g;
+    SS *p;
+    const SS *v[3];
+    SP *psi[kMaxMech];
+    SS *psip[3];
+    const SS *kdt;               // K dt per voxel
+    const SS *b2dt;              // 2 beta dt per voxel, or null (linear)
+    const uint16_t *cls;
+    const R *lut;
+    const R *pd[3], *pa[3];      // absorbing profile at integer points per axis
+    Monitor *mon;
+};
+
+template <typename SS, typename R>
+__device__ __forceinline__ void ld4_or_zero(const SS *base, bool ok, R (&v)[4])
+{
+    if (ok) Io<SS>::ldg(base, v);
+    else v[0] = v[1] = v[2] = v[3] = R(0);
+}
+
+// ---------------------------------------------------------------------------
+// velocity sweep
+
+template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY>
+__global__ void __launch_bounds__(BX *BY)
+k_velocity(const VelArgs<R, SS, SP> A)
+{
+    constexpr int TW = 4 * BX;
+    constexpr int SW = TW + 8;                 // 4 halo columns each side
+    constexpr int SH = DIM == 3 ? BY + 7 : BY; // 3 rows below, 4 above
+    constexpr int RO = DIM == 3 ? 3 : 0;       // smem row of the tile's first row
+    __shared__ __align__(16) R sp[2][SH][SW];
+    __shared__ __align__(16) R sr[2][BY + 1][TW + 4];
+
+    const Geo<R> &G = A.g;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int xb = blockIdx.x * TW, yb = blockIdx.y * BY;
+    const int x0 = xb + 4 * tx, y = yb + ty;
+    const int z0 = blockIdx.z * G.zseg;
+    const int z1 = min(G.nz, z0 + G.zseg);
+    const bool hd = (x0 < G.nx) && (y < G.ny);
+    const long long row = (long long)y * G.px + x0;
+
+    R q[8][4];      // p of own columns, planes k-3 .. k+4
+    R rq[2][4];     // rho of own columns, planes k, k+1
+#pragma unroll
+    for (int j = 0; j < 7; ++j) {
+        const int kk = z0 - 3 + j;
+        ld4_or_zero(A.p + kk * G.plane + row, hd && kk >= 0 && kk < G.nz, q[j]);
+    }
+    ld4_or_zero(A.rho + z0 * G.plane + row, hd && z0 < G.nz, rq[0]);
+
+    for (int k = z0; k < z1; ++k) {
+        const long long pk = (long long)k * G.plane;
+        const int buf = k & 1;
+        // ---- global loads of this plane (issued before the barrier) ----
+        ld4_or_zero(A.p + pk + 4 * G.plane + row, hd && k + 4 < G.nz, q[7]);
+        ld4_or_zero(A.rho + pk + G.plane + row, hd && k + 1 < G.nz, rq[1]);
+        R hx[4];         // x-halo of p (edge threads)
+        const bool left = (tx == 0), right = (tx == BX - 1);
+        if (left) ld4_or_zero(A.p + pk + (long long)y * G.px + (x0 - 4), y < G.ny && x0 - 4 >= 0, hx);
+        else if (right) ld4_or_zero(A.p + pk + (long long)y * G.px + (x0 + 4), y < G.ny && x0 + 4 < G.px, hx);
+        R hy[4];         // y-halo row of p (rows ty < 7)
+        int hrow = -1;
+        if (DIM == 3 && ty < 7) {
+            const int r = ty;
+            const int yy = r < 3 ? yb - 3 + r : yb + BY + (r - 3);
+            hrow = r < 3 ? r : BY + 3 + (r - 3);
+            ld4_or_zero(A.p + pk + (long long)yy * G.px + x0, yy >= 0 && yy < G.ny && x0 < G.px, hy);
+        }
+        R rhx = R(0);    // rho right of the tile
+        if (right && xb + TW < G.nx && y < G.ny) rhx = A.rho[pk + (long long)y * G.px + xb + TW];
+        R rhy[4];        // rho of the row above the tile
+        if (DIM == 3 && ty == 0)
+            ld4_or_zero(A.rho + pk + (long long)(yb + BY) * G.px + x0, yb + BY < G.ny && x0 < G.px, rhy);
+        uint2 cl = make_uint2(0, 0);
+        if (hd) cl = __ldg(reinterpret_cast<const uint2 *>(A.cls + pk + row));
+        R vv[3][4];
+        R ps[NM][3][4];
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            if (DIM == 2 && ax == 1) continue;
+            if (hd) Io<SS>::ld(A.v[ax] + pk + row, vv[ax]);
+#pragma unroll
+            for (int m = 0; m < NM; ++m)
+                if (hd) Io<SP>::ld(A.psi[m][ax] + pk + row, ps[m][ax]);
+        }
+        // ---- shared-memory tiles of plane k ----
+        {
+            R *dst = &sp[buf][RO + ty][4 + 4 * tx];
+            dst[0] = q[3][0]; dst[1] = q[3][1]; dst[2] = q[3][2]; dst[3] = q[3][3];
+            if (left) { R *h = &sp[buf][RO + ty][0]; h[0] = hx[0]; h[1] = hx[1]; h[2] = hx[2]; h[3] = hx[3]; }
+            if (right) { R *h = &sp[buf][RO + ty][TW + 4]; h[0] = hx[0]; h[1] = hx[1]; h[2] = hx[2]; h[3] = hx[3]; }
+            if (DIM == 3 && hrow >= 0) {
+                R *h = &sp[buf][hrow][4 + 4 * tx];
+                h[0] = hy[0]; h[1] = hy[1]; h[2] = hy[2]; h[3] = hy[3];
+            }
+            R *r = &sr[buf][ty][4 * tx];
+            r[0] = rq[0][0]; r[1] = rq[0][1]; r[2] = rq[0][2]; r[3] = rq[0][3];
+            if (right) sr[buf][ty][TW] = rhx;
+            if (DIM == 3 && ty == 0) {
+                R *h = &sr[buf][BY][4 * tx];
+                h[0] = rhy[0]; h[1] = rhy[1]; h[2] = rhy[2]; h[3] = rhy[3];
+            }
+        }
+        __syncthreads();
+        if (hd) {
+            // ---- derivatives ----
+            R g[3][4];
+            {
+                R w[12];
+                const R *s = &sp[buf][RO + ty][4 * tx];
+#pragma unroll
+                for (int i = 0; i < 12; ++i) w[i] = s[i];
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    g[0][e] = G.c1 * (w[e + 5] - w[e + 4]) + G.c2 * (w[e + 6] - w[e + 3]) +
+                              G.c3 * (w[e + 7] - w[e + 2]) + G.c4 * (w[e + 8] - w[e + 1]);
+            }
+            if (DIM == 3) {
+                R c[8][4];
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    const R *s = &sp[buf][ty + r][4 + 4 * tx];
+                    c[r][0] = s[0]; c[r][1] = s[1]; c[r][2] = s[2]; c[r][3] = s[3];
+                }
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    g[1][e] = G.c1 * (c[4][e] - c[3][e]) + G.c2 * (c[5][e] - c[2][e]) +
+                              G.c3 * (c[6][e] - c[1][e]) + G.c4 * (c[7][e] - c[0][e]);
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                g[2][e] = G.c1 * (q[4][e] - q[3][e]) + G.c2 * (q[5][e] - q[2][e]) +
+                          G.c3 * (q[6][e] - q[1][e]) + G.c4 * (q[7][e] - q[0][e]);
+            // ---- face densities -> dt / rho_face ----
+            R dtr[3][4];
+            {
+                const R *r0 = &sr[buf][ty][4 * tx];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const R own = r0[e];
+                    const R nxr = (x0 + e + 1 < G.nx) ? r0[e + 1] : own;
+                    dtr[0][e] = R(2) * G.dt / (own + nxr);
+                    if (DIM == 3) {
+                        const R nyr = (y + 1 < G.ny) ? sr[buf][ty + 1][4 * tx + e] : own;
+                        dtr[1][e] = R(2) * G.dt / (own + nyr);
+                    }
+                    const R nzr = (k + 1 < G.nz) ? rq[1][e] : own;
+                    dtr[2][e] = R(2) * G.dt / (own + nzr);
+                }
+            }
+            const uint16_t cls4[4] = {(uint16_t)(cl.x & 0xffffu), (uint16_t)(cl.x >> 16),
+                                      (uint16_t)(cl.y & 0xffffu), (uint16_t)(cl.y >> 16)};
+            // ---- updates, element by element (class coefficients cached) ----
+            R hdr[4], A1[4], B1[4], H1[4];
+            int cprev = -1;
+            const bool pml_x = G.wabs > 0 && (x0 < G.wabs || x0 + 3 >= G.nx - G.wabs);
+            const bool pml_y = DIM == 3 && G.wabs > 0 && (y < G.wabs || y >= G.ny - G.wabs);
+            const bool pml_z = G.wabs > 0 && (k < G.wabs || k >= G.nz - G.wabs);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int c = cls4[e];
+                if (c != cprev) {
+                    lut4(A.lut, c, 0, hdr);
+                    lut4(A.lut, c, kLutA1, A1);
+                    lut4(A.lut, c, kLutB1, B1);
+                    lut4(A.lut, c, kLutH1, H1);
+                    cprev = c;
+                }
+                const bool live = x0 + e < G.nx;
+#pragma unroll
+                for (int ax = 0; ax < 3; ++ax) {
+                    if (DIM == 2 && ax == 1) continue;
+                    const R gd = g[ax][e];
+                    R st = gd * hdr[2];
+#pragma unroll
+                    for (int m = 0; m < NM; ++m) {
+                        const R po = ps[m][ax][e];
+                        st += H1[m] * po;
+                        ps[m][ax][e] = live ? B1[m] * po + A1[m] * gd : R(0);
+                    }
+                    const bool pml_here = ax == 0 ? pml_x : (ax == 1 ? pml_y : pml_z);
+                    if (pml_here) {
+                        const int pos = ax == 0 ? x0 + e : (ax == 1 ? y : k);
+                        const R d = A.pd[ax][pos];
+                        if (d > R(0) && live) {
+                            R a, b;
+                            pml_ab(d, A.pa[ax][pos], hdr[0], G.dt, a, b);
+                            SS *pp = A.psip[ax] + pk + row + e;
+                            const R po = Io<SS>::ld1(pp);
+                            st += R(0.5) * (R(1) + b) * po + R(0.5) * a * gd;
+                            Io<SS>::st1(pp, SS(b * po + a * gd));
+                        }
+                    }
+                    vv[ax][e] = live ? vv[ax][e] - dtr[ax][e] * st : R(0);
+                }
+            }
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax) {
+                if (DIM == 2 && ax == 1) continue;
+                Io<SS>::st(A.v[ax] + pk + row, vv[ax]);
+#pragma unroll
+                for (int m = 0; m < NM; ++m) Io<SP>::st(A.psi[m][ax] + pk + row, ps[m][ax]);
+            }
+        }
+        // ---- advance the queues ----
+#pragma unroll
+        for (int j = 0; j < 7; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) q[j][e] = q[j + 1][e];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) rq[0][e] = rq[1][e];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// pressure sweep
+
+template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY, bool NL>
+__global__ void __launch_bounds__(BX *BY)
+k_pressure(const PresArgs<R, SS, SP> A)
+{
+    constexpr int TW = 4 * BX;
+    constexpr int SWX = TW + 8;                  // vx row with 4 halo columns each side
+    constexpr int SHY = DIM == 3 ? BY + 7 : 1;   // vy rows: 4 below, 3 above
+    __shared__ __align__(16) R svx[2][BY][SWX];
+    __shared__ __align__(16) R svy[2][SHY][TW];
+
+    const Geo<R> &G = A.g;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int xb = blockIdx.x * TW, yb = blockIdx.y * BY;
+    const int x0 = xb + 4 * tx, y = yb + ty;
+    const int z0 = blockIdx.z * G.zseg;
+    const int z1 = min(G.nz, z0 + G.zseg);
+    const bool hd = (x0 < G.nx) && (y < G.ny);
+    const long long row = (long long)y * G.px + x0;
+
+    R qz[8][4];     // vz of own columns, planes k-4 .. k+3
+#pragma unroll
+    for (int j = 0; j < 7; ++j) {
+        const int kk = z0 - 4 + j;
+        ld4_or_zero(A.v[2] + kk * G.plane + row, hd && kk >= 0 && kk < G.nz, qz[j]);
+    }
+    R pmax = R(0);
+    bool bad = false;
+
+    for (int k = z0; k < z1; ++k) {
+        const long long pk = (long long)k * G.plane;
+        const int buf = k & 1;
+        ld4_or_zero(A.v[2] + pk + 3 * G.plane + row, hd && k + 3 < G.nz, qz[7]);
+        R cx[4], hx[4];
+        ld4_or_zero(A.v[0] + pk + row, hd, cx);
+        const bool left = (tx == 0), right = (tx == BX - 1);
+        if (left) ld4_or_zero(A.v[0] + pk + (long long)y * G.px + (x0 - 4), y < G.ny && x0 - 4 >= 0, hx);
+        else if (right) ld4_or_zero(A.v[0] + pk + (long long)y * G.px + (x0 + 4), y < G.ny && x0 + 4 < G.px, hx);
+        R cy[4], hy[4];
+        int hrow = -1;
+        if (DIM == 3) {
+            ld4_or_zero(A.v[1] + pk + row, hd, cy);
+            if (ty < 7) {
+                const int r = ty;
+                const int yy = r < 4 ? yb - 4 + r : yb + BY + (r - 4);
+                hrow = r < 4 ? r : BY + 4 + (r - 4);
+                ld4_or_zero(A.v[1] + pk + (long long)yy * G.px + x0, yy >= 0 && yy < G.ny && x0 < G.px, hy);
+            }
+        }
+        R pv[4], kd[4], bd[4];
+        R ps[NM][4];
+        uint2 cl = make_uint2(0, 0);
+        if (hd) {
+            Io<SS>::ld(A.p + pk + row, pv);
+            Io<SS>::ldg(A.kdt + pk + row, kd);
+            if (NL) Io<SS>::ldg(A.b2dt + pk + row, bd);
+            cl = __ldg(reinterpret_cast<const uint2 *>(A.cls + pk + row));
+#pragma unroll
+            for (int m = 0; m < NM; ++m) Io<SP>::ld(A.psi[m] + pk + row, ps[m]);
+        }
+        {
+            R *d = &svx[buf][ty][4 + 4 * tx];
+            d[0] = cx[0]; d[1] = cx[1]; d[2] = cx[2]; d[3] = cx[3];
+            if (left) { R *h = &svx[buf][ty][0]; h[0] = hx[0]; h[1] = hx[1]; h[2] = hx[2]; h[3] = hx[3]; }
+            if (right) { R *h = &svx[buf][ty][TW + 4]; h[0] = hx[0]; h[1] = hx[1]; h[2] = hx[2]; h[3] = hx[3]; }
+            if (DIM == 3) {
+                R *c = &svy[buf][4 + ty][4 * tx];
+                c[0] = cy[0]; c[1] = cy[1]; c[2] = cy[2]; c[3] = cy[3];
+                if (hrow >= 0) { R *h = &svy[buf][hrow][4 * tx]; h[0] = hy[0]; h[1] = hy[1]; h[2] = hy[2]; h[3] = hy[3]; }
+            }
+        }
+        __syncthreads();
+        if (hd) {
+            R qd[3][4];
+            {
+                R w[12];
+                const R *s = &svx[buf][ty][4 * tx];
+#pragma unroll
+                for (int i = 0; i < 12; ++i) w[i] = s[i];
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    qd[0][e] = G.c1 * (w[e + 4] - w[e + 3]) + G.c2 * (w[e + 5] - w[e + 2]) +
+                               G.c3 * (w[e + 6] - w[e + 1]) + G.c4 * (w[e + 7] - w[e + 0]);
+            }
+            if (DIM == 3) {
+                R c[8][4];
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    const R *s = &svy[buf][ty + r][4 * tx];
+                    c[r][0] = s[0]; c[r][1] = s[1]; c[r][2] = s[2]; c[r][3] = s[3];
+                }
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    qd[1][e] = G.c1 * (c[4][e] - c[3][e]) + G.c2 * (c[5][e] - c[2][e]) +
+                               G.c3 * (c[6][e] - c[1][e]) + G.c4 * (c[7][e] - c[0][e]);
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                qd[2][e] = G.c1 * (qz[4][e] - qz[3][e]) + G.c2 * (qz[5][e] - qz[2][e]) +
+                           G.c3 * (qz[6][e] - qz[1][e]) + G.c4 * (qz[7][e] - qz[0][e]);
+            const uint16_t cls4[4] = {(uint16_t)(cl.x & 0xffffu), (uint16_t)(cl.x >> 16),
+                                      (uint16_t)(cl.y & 0xffffu), (uint16_t)(cl.y >> 16)};
+            R hdr[4], A2[4], B2[4], H2[4];
+            int cprev = -1;
+            const bool pml_x = G.wabs > 0 && (x0 < G.wabs || x0 + 3 >= G.nx - G.wabs);
+            const bool pml_y = DIM == 3 && G.wabs > 0 && (y < G.wabs || y >= G.ny - G.wabs);
+            const bool pml_z = G.wabs > 0 && (k < G.wabs || k >= G.nz - G.wabs);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int c = cls4[e];
+                if (c != cprev) {
+                    lut4(A.lut, c, 0, hdr);
+                    lut4(A.lut, c, kLutA2, A2);
+                    lut4(A.lut, c, kLutB2, B2);
+                    lut4(A.lut, c, kLutH2, H2);
+                    cprev = c;
+                }
+                const bool live = x0 + e < G.nx;
+                R div = qd[0][e] + qd[2][e];
+                if (DIM == 3) div += qd[1][e];
+                R st = div * hdr[3];
+#pragma unroll
+                for (int m = 0; m < NM; ++m) {
+                    const R po = ps[m][e];
+                    st += H2[m] * po;
+                    ps[m][e] = live ? B2[m] * po + A2[m] * div : R(0);
+                }
+#pragma unroll
+                for (int ax = 0; ax < 3; ++ax) {
+                    if (DIM == 2 && ax == 1) continue;
+                    const bool pml_here = ax == 0 ? pml_x : (ax == 1 ? pml_y : pml_z);
+                    if (!pml_here) continue;
+                    const int pos = ax == 0 ? x0 + e : (ax == 1 ? y : k);
+                    const R d = A.pd[ax][pos];
+                    if (d > R(0) && live) {
+                        R a, b;
+                        pml_ab(d, A.pa[ax][pos], hdr[1], G.dt, a, b);
+                        SS *pp = A.psip[ax] + pk + row + e;
+                        const R po = Io<SS>::ld1(pp);
+                        st += R(0.5) * (R(1) + b) * po + R(0.5) * a * qd[ax][e];
+                        Io<SS>::st1(pp, SS(b * po + a * qd[ax][e]));
+                    }
+                }
+                R fac = kd[e];
+                if (NL) fac += bd[e] * pv[e];
+                const R pn = live ? pv[e] - fac * st : R(0);
+                pv[e] = pn;
+                const R ap = fabs(pn);
+                bad |= !(ap <= R(3.0e38));
+                pmax = fmax(pmax, ap);
+            }
+            Io<SS>::st(A.p + pk + row, pv);
+#pragma unroll
+            for (int m = 0; m < NM; ++m) Io<SP>::st(A.psi[m] + pk + row, ps[m]);
+        }
+#pragma unroll
+        for (int j = 0; j < 7; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) qz[j][e] = qz[j + 1][e];
+    }
+    // ---- stability monitor: one atomic per warp ----
+    float m = bad ? 0.0f : (float)fmin(pmax, R(3.0e38));
+    unsigned any_bad = __ballot_sync(0xffffffffu, bad);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x + threadIdx.y * BX) % 32 == 0) {
+        if (m > 0.0f) atomicMax(&A.mon->max_bits, __float_as_uint(m));
+        if (any_bad) atomicExch(&A.mon->nonfinite, 1);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// sources, receivers, step counter
+
+template <typename SS, typename R>
+__global__ void k_sources(SS *p, const long long *idx, const R *gain, const int *wave_of,
+                          const R *waves, int wave_len, int n_src, const int *d_it, int j)
+{
+    const int it = *d_it + j;
+    if (it >= wave_len) return;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n_src; s += gridDim.x * blockDim.x)
+        p[idx[s]] = SS(R(p[idx[s]]) + gain[s] * waves[(size_t)wave_of[s] * wave_len + it]);
+}
+
+template <typename SS>
+__global__ void k_receivers(const SS *p, const long long *idx, SS *traces, int n_rcv, int n_rec,
+                            int decim, const int *d_it, int j)
+{
+    const int it = *d_it + j;
+    if (it % decim != 0 || it / decim >= n_rec) return;
+    const int col = it / decim;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n_rcv; r += gridDim.x * blockDim.x)
+        traces[(size_t)r * n_rec + col] = p[idx[r]];
+}
+
+__global__ void k_advance(int *d_it, int n);
+
+}  // namespace fwgb

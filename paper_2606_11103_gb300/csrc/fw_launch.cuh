@@ -1,0 +1,113 @@
+// Launch helpers: build kernel arguments from a medium and dispatch the
+// template instance for (dimension, mechanisms, nonlinearity).  Included by
+// one translation unit per storage type so that they compile in parallel.
+#pragma once
+
+#include "fw_kernels.cuh"
+
+namespace fwgb {
+
+template <typename R> struct Tile3 { static constexpr int BX = sizeof(R) == 8 ? 16 : 32, BY = 8; };
+template <typename R> struct Tile2 { static constexpr int BX = 64, BY = 1; };
+
+template <typename R> Geo<R> make_geo(const fw_medium *m)
+{
+    Geo<R> g{};
+    g.nx = m->NX;
+    g.ny = m->NY;
+    g.nz = m->NZ;
+    g.px = m->px;
+    g.plane = (long long)m->plane;
+    g.zseg = m->zseg;
+    g.wabs = m->wabs;
+    // 8th-order staggered weights (Taylor) divided by dx
+    const double cm[4] = {1225.0 / 1024.0, -245.0 / 3072.0, 49.0 / 5120.0, -5.0 / 7168.0};
+    g.c1 = R(cm[0] / m->dx);
+    g.c2 = R(cm[1] / m->dx);
+    g.c3 = R(cm[2] / m->dx);
+    g.c4 = R(cm[3] / m->dx);
+    g.dt = R(m->dt);
+    return g;
+}
+
+// which: bit 0 = velocity sweep, bit 1 = pressure sweep
+template <typename R, typename SS, typename SP, int DIM, int NM>
+cudaError_t launch_dn(const fw_medium *m, cudaStream_t s, int which)
+{
+    constexpr int BX = DIM == 3 ? Tile3<R>::BX : Tile2<R>::BX;
+    constexpr int BY = DIM == 3 ? Tile3<R>::BY : Tile2<R>::BY;
+    const Geo<R> g = make_geo<R>(m);
+    dim3 block(BX, BY);
+    dim3 grid((m->NX + 4 * BX - 1) / (4 * BX), (m->NY + BY - 1) / BY, (m->NZ + m->zseg - 1) / m->zseg);
+
+    VelArgs<R, SS, SP> va{};
+    va.g = g;
+    va.p = static_cast<const SS *>(m->p);
+    for (int ax = 0; ax < 3; ++ax) {
+        va.v[ax] = static_cast<SS *>(m->v[ax]);
+        va.psip[ax] = static_cast<SS *>(m->psi1p[ax]);
+        va.pd[ax] = static_cast<const R *>(m->prof[ax][0]);
+        va.pa[ax] = static_cast<const R *>(m->prof[ax][1]);
+        for (int n = 0; n < NM; ++n) va.psi[n][ax] = static_cast<SP *>(m->psi1[n][ax]);
+    }
+    va.rho = static_cast<const SS *>(m->rho);
+    va.cls = m->cls;
+    va.lut = static_cast<const R *>(m->lut);
+    if (which & 1) k_velocity<R, SS, SP, DIM, NM, BX, BY><<<grid, block, 0, s>>>(va);
+    if (!(which & 2)) return cudaGetLastError();
+
+    PresArgs<R, SS, SP> pa{};
+    pa.g = g;
+    pa.p = static_cast<SS *>(m->p);
+    for (int ax = 0; ax < 3; ++ax) {
+        pa.v[ax] = static_cast<const SS *>(m->v[ax]);
+        pa.psip[ax] = static_cast<SS *>(m->psi2p[ax]);
+        pa.pd[ax] = static_cast<const R *>(m->prof[ax][2]);
+        pa.pa[ax] = static_cast<const R *>(m->prof[ax][3]);
+    }
+    for (int n = 0; n < NM; ++n) pa.psi[n] = static_cast<SP *>(m->psi2[n]);
+    pa.kdt = static_cast<const SS *>(m->kdt);
+    pa.b2dt = static_cast<const SS *>(m->b2dt);
+    pa.cls = m->cls;
+    pa.lut = static_cast<const R *>(m->lut);
+    pa.mon = m->mon;
+    if (m->nonlinear)
+        k_pressure<R, SS, SP, DIM, NM, BX, BY, true><<<grid, block, 0, s>>>(pa);
+    else
+        k_pressure<R, SS, SP, DIM, NM, BX, BY, false><<<grid, block, 0, s>>>(pa);
+    return cudaGetLastError();
+}
+
+template <typename R, typename SS, typename SP>
+cudaError_t launch_sweeps(const fw_medium *m, cudaStream_t s, int which)
+{
+    const bool d3 = m->ndim == 3;
+    switch (m->nmech) {
+    case 1: return d3 ? launch_dn<R, SS, SP, 3, 1>(m, s, which) : launch_dn<R, SS, SP, 2, 1>(m, s, which);
+    case 2: return d3 ? launch_dn<R, SS, SP, 3, 2>(m, s, which) : launch_dn<R, SS, SP, 2, 2>(m, s, which);
+    case 3: return d3 ? launch_dn<R, SS, SP, 3, 3>(m, s, which) : launch_dn<R, SS, SP, 2, 3>(m, s, which);
+    case 4: return d3 ? launch_dn<R, SS, SP, 3, 4>(m, s, which) : launch_dn<R, SS, SP, 2, 4>(m, s, which);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename R, typename SS>
+cudaError_t launch_io(const fw_medium *m, int j, cudaStream_t s)
+{
+    if (m->n_src > 0) {
+        int nb = (m->n_src + 255) / 256;
+        k_sources<SS, R><<<nb, 256, 0, s>>>(static_cast<SS *>(m->p), m->src_idx,
+                                            static_cast<const R *>(m->src_gain), m->wave_of,
+                                            static_cast<const R *>(m->waves), m->wave_len, m->n_src,
+                                            m->d_it, j);
+    }
+    if (m->n_rcv > 0) {
+        int nb = (m->n_rcv + 255) / 256;
+        k_receivers<SS><<<nb, 256, 0, s>>>(static_cast<const SS *>(m->p), m->rcv_idx,
+                                           static_cast<SS *>(m->traces), m->n_rcv, m->n_rec,
+                                           m->decim, m->d_it, j);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace fwgb
