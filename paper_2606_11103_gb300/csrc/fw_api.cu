@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -29,6 +30,8 @@ using namespace fwgb;
     } while (0)
 
 namespace {
+
+cudaError_t launch_sweep(const fw_medium *m, cudaStream_t s, int which);
 
 // ---- allocator --------------------------------------------------------------
 std::mutex g_alloc_mu;
@@ -495,6 +498,11 @@ std::vector<long long> mask_to_index(const fw_medium *m, const uint8_t *mask)
 
 int choose_zseg(const fw_medium *m)
 {
+    // tuning override: FWGB_ZSEG planes per CTA (8..1024)
+    if (const char *e = std::getenv("FWGB_ZSEG")) {
+        int z = std::atoi(e);
+        if (z >= 8 && z <= 1024) return z;
+    }
     // enough CTAs for several waves over 152 SMs, at least 16 planes per CTA
     const int tw = m->ndim == 3 ? (m->es == 8 ? 64 : 128) : 256;
     const int by = m->ndim == 3 ? 8 : 1;
@@ -641,6 +649,7 @@ int create_common(const fw_grid *g, const float *c, const float *rho, const floa
         }
     }
     if (cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking) != cudaSuccess) { release(m); return FW_ERR_CUDA; }
+    if (launch_sweep(m, s, 4) != cudaSuccess) { release(m); return FW_ERR_CUDA; }
     if (cudaStreamSynchronize(s) != cudaSuccess) { release(m); return FW_ERR_CUDA; }
     m->last_stream = s;
     *out = m;

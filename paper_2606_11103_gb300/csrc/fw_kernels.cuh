@@ -142,6 +142,76 @@ __device__ __forceinline__ void pml_ab(R d, R al, R kappa, R dt, R &a, R &b)
 }
 
 // ---------------------------------------------------------------------------
+// asynchronous global -> shared copies (cp.async, zero fill when !ok)
+
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *sdst, const void *gsrc, bool ok)
+{
+    const unsigned d = smem_u32(sdst);
+    const int n = ok ? BYTES : 0;
+    if (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gsrc), "r"(n) : "memory");
+    else if (BYTES == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(gsrc), "r"(n) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(gsrc), "r"(n) : "memory");
+}
+
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+template <int N> __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// copy the 4 consecutive elements of type S at gsrc (16 or 8 bytes, or two
+// 16-byte pieces for double)
+template <typename S>
+__device__ __forceinline__ void cp_async4(S *sdst, const S *gsrc, bool ok)
+{
+    if (sizeof(S) == 4) cp_async<16>(sdst, gsrc, ok);
+    else if (sizeof(S) == 2) cp_async<8>(sdst, gsrc, ok);
+    else { cp_async<16>(sdst, gsrc, ok); cp_async<16>(sdst + 2, gsrc + 2, ok); }
+}
+
+// 4 consecutive elements of type S from shared memory, as R
+template <typename S> struct Sm;
+template <> struct Sm<float> {
+    template <typename R> static __device__ __forceinline__ void ld(const float *p, R (&v)[4])
+    {
+        float4 t = *reinterpret_cast<const float4 *>(p);
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    }
+};
+template <> struct Sm<double> {
+    template <typename R> static __device__ __forceinline__ void ld(const double *p, R (&v)[4])
+    {
+        double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+};
+template <> struct Sm<__nv_bfloat16> {
+    template <typename R> static __device__ __forceinline__ void ld(const __nv_bfloat16 *p, R (&v)[4])
+    {
+        uint2 t = *reinterpret_cast<const uint2 *>(p);
+        float2 a = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&t.x));
+        float2 b = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&t.y));
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+};
+template <> struct Sm<__half> {
+    template <typename R> static __device__ __forceinline__ void ld(const __half *p, R (&v)[4])
+    {
+        uint2 t = *reinterpret_cast<const uint2 *>(p);
+        float2 a = __half22float2(*reinterpret_cast<__half2 *>(&t.x));
+        float2 b = __half22float2(*reinterpret_cast<__half2 *>(&t.y));
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+};
+
+// ---------------------------------------------------------------------------
 // launch parameters
 
 template <typename R> struct Geo {
@@ -188,18 +258,112 @@ __device__ __forceinline__ void ld4_or_zero(const SS *base, bool ok, R (&v)[4])
 }
 
 // ---------------------------------------------------------------------------
+// shared-memory layout of the sweeps (dynamic shared memory)
+//
+// Each sweep keeps two stages: while plane k is computed from stage k&1,
+// cp.async copies of plane k+1 fill stage (k+1)&1, so one plane of every
+// stream is always in flight.  A stage holds, per stream, the CTA tile
+// [BY][4*BX] in the storage type; the derivative tiles (with halos) are
+// double-buffered by plane parity as well.
+
+template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY> struct VelSmem {
+    static constexpr int TW = 4 * BX, SW = TW + 8, SH = DIM == 3 ? BY + 7 : BY, RO = DIM == 3 ? 3 : 0;
+    static constexpr int NAX = DIM == 3 ? 3 : 2;
+    static constexpr size_t TILE = (size_t)BY * TW;
+    // per stage (bytes, 16-aligned pieces)
+    static constexpr size_t o_v = 0;
+    static constexpr size_t o_psi = o_v + 3 * TILE * sizeof(SS);
+    static constexpr size_t o_pn = o_psi + (size_t)NM * 3 * TILE * sizeof(SP);
+    static constexpr size_t o_rn = o_pn + TILE * sizeof(SS);
+    static constexpr size_t o_cls = o_rn + TILE * sizeof(SS);
+    static constexpr size_t stage = (o_cls + TILE * 2 + 127) / 128 * 128;
+    // derivative tiles
+    static constexpr size_t o_sp = 2 * stage;
+    static constexpr size_t o_sr = o_sp + 2 * (size_t)SH * SW * sizeof(R);
+    static constexpr size_t bytes = o_sr + 2 * (size_t)(BY + 1) * (TW + 4) * sizeof(R);
+};
+
+template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY> struct PresSmem {
+    static constexpr int TW = 4 * BX, SWX = TW + 8, SHY = DIM == 3 ? BY + 7 : 1;
+    static constexpr size_t TILE = (size_t)BY * TW;
+    static constexpr size_t o_qn = 0;
+    static constexpr size_t o_p = o_qn + TILE * sizeof(SS);
+    static constexpr size_t o_kd = o_p + TILE * sizeof(SS);
+    static constexpr size_t o_bd = o_kd + TILE * sizeof(SS);
+    static constexpr size_t o_psi = o_bd + TILE * sizeof(SS);
+    static constexpr size_t o_cls = o_psi + (size_t)NM * TILE * sizeof(SP);
+    static constexpr size_t stage = (o_cls + TILE * 2 + 127) / 128 * 128;
+    static constexpr size_t o_svx = 2 * stage;
+    static constexpr size_t o_svy = o_svx + 2 * (size_t)BY * SWX * sizeof(R);
+    static constexpr size_t bytes = o_svy + 2 * (size_t)SHY * TW * sizeof(R);
+};
+
+// ---------------------------------------------------------------------------
 // velocity sweep
 
 template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY>
-__global__ void __launch_bounds__(BX *BY)
+__device__ __forceinline__ void vel_issue(const VelArgs<R, SS, SP> &A, unsigned char *sm, int k, int x0, int y,
+                                          int xb, int yb, long long row, bool hd)
+{
+    using L = VelSmem<R, SS, SP, DIM, NM, BX, BY>;
+    const Geo<R> &G = A.g;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const long long pk = (long long)k * G.plane;
+    unsigned char *st = sm + (k & 1) * L::stage;
+    const int e0 = ty * L::TW + 4 * tx;       // this thread's element offset in a stage tile
+    const SS *gz = A.p;                       // any valid address for zero-fill copies
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        if (DIM == 2 && ax == 1) continue;
+        cp_async4(reinterpret_cast<SS *>(st + L::o_v) + ax * L::TILE + e0, hd ? A.v[ax] + pk + row : gz, hd);
+#pragma unroll
+        for (int m = 0; m < NM; ++m)
+            cp_async4(reinterpret_cast<SP *>(st + L::o_psi) + (m * 3 + ax) * L::TILE + e0,
+                      hd ? A.psi[m][ax] + pk + row : reinterpret_cast<const SP *>(gz), hd);
+    }
+    {
+        const bool ok = hd && k + 4 < G.nz;
+        cp_async4(reinterpret_cast<SS *>(st + L::o_pn) + e0, ok ? A.p + pk + 4 * G.plane + row : gz, ok);
+        const bool okr = hd && k + 1 < G.nz;
+        cp_async4(reinterpret_cast<SS *>(st + L::o_rn) + e0, okr ? A.rho + pk + G.plane + row : gz, okr);
+        cp_async<8>(reinterpret_cast<uint16_t *>(st + L::o_cls) + e0, hd ? (const void *)(A.cls + pk + row) : (const void *)gz, hd);
+    }
+    // halos of plane k straight into the derivative tiles of parity k&1
+    R *sp = reinterpret_cast<R *>(sm + L::o_sp) + (k & 1) * L::SH * L::SW;
+    R *sr = reinterpret_cast<R *>(sm + L::o_sr) + (k & 1) * (BY + 1) * (L::TW + 4);
+    if (tx == 0) {
+        const bool ok = y < G.ny && x0 - 4 >= 0;
+        cp_async4(reinterpret_cast<SS *>(sp + (L::RO + ty) * L::SW), ok ? A.p + pk + (long long)y * G.px + (x0 - 4) : gz, ok);
+    }
+    if (tx == BX - 1) {
+        const bool ok = y < G.ny && x0 + 4 < G.px;
+        cp_async4(reinterpret_cast<SS *>(sp + (L::RO + ty) * L::SW + L::TW + 4),
+                  ok ? A.p + pk + (long long)y * G.px + (x0 + 4) : gz, ok);
+        const bool okr = y < G.ny && xb + L::TW < G.nx;
+        cp_async<sizeof(SS)>(reinterpret_cast<SS *>(sr + ty * (L::TW + 4) + L::TW),
+                             okr ? A.rho + pk + (long long)y * G.px + xb + L::TW : gz, okr);
+    }
+    if (DIM == 3 && ty < 7) {
+        const int yy = ty < 3 ? yb - 3 + ty : yb + BY + (ty - 3);
+        const int hrow = ty < 3 ? ty : BY + 3 + (ty - 3);
+        const bool ok = yy >= 0 && yy < G.ny && x0 < G.px;
+        cp_async4(reinterpret_cast<SS *>(sp + hrow * L::SW + 4 + 4 * tx), ok ? A.p + pk + (long long)yy * G.px + x0 : gz, ok);
+    }
+    if (DIM == 3 && ty == 0) {
+        const bool ok = yb + BY < G.ny && x0 < G.px;
+        cp_async4(reinterpret_cast<SS *>(sr + BY * (L::TW + 4) + 4 * tx), ok ? A.rho + pk + (long long)(yb + BY) * G.px + x0 : gz, ok);
+    }
+}
+
+template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY>
+__global__ void __launch_bounds__(BX *BY, 1)
 k_velocity(const VelArgs<R, SS, SP> A)
 {
-    constexpr int TW = 4 * BX;
-    constexpr int SW = TW + 8;                 // 4 halo columns each side
-    constexpr int SH = DIM == 3 ? BY + 7 : BY; // 3 rows below, 4 above
-    constexpr int RO = DIM == 3 ? 3 : 0;       // smem row of the tile's first row
-    __shared__ __align__(16) R sp[2][SH][SW];
-    __shared__ __align__(16) R sr[2][BY + 1][TW + 4];
+    using L = VelSmem<R, SS, SP, DIM, NM, BX, BY>;
+    constexpr int TW = L::TW, SW = L::SW, SH = L::SH, RO = L::RO;
+    static_assert(DIM == 2 || BY >= 7, "the y halo needs 7 thread rows");
+    static_assert(sizeof(SS) == sizeof(R), "state is stored in the arithmetic type");
+    extern __shared__ __align__(128) unsigned char smem[];
 
     const Geo<R> &G = A.g;
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -209,6 +373,7 @@ k_velocity(const VelArgs<R, SS, SP> A)
     const int z1 = min(G.nz, z0 + G.zseg);
     const bool hd = (x0 < G.nx) && (y < G.ny);
     const long long row = (long long)y * G.px + x0;
+    const int e0 = ty * TW + 4 * tx;
 
     R q[8][4];      // p of own columns, planes k-3 .. k+4
     R rq[2][4];     // rho of own columns, planes k, k+1
@@ -218,67 +383,33 @@ k_velocity(const VelArgs<R, SS, SP> A)
         ld4_or_zero(A.p + kk * G.plane + row, hd && kk >= 0 && kk < G.nz, q[j]);
     }
     ld4_or_zero(A.rho + z0 * G.plane + row, hd && z0 < G.nz, rq[0]);
+    if (z0 < z1) vel_issue<R, SS, SP, DIM, NM, BX, BY>(A, smem, z0, x0, y, xb, yb, row, hd);
+    cp_commit();
 
     for (int k = z0; k < z1; ++k) {
         const long long pk = (long long)k * G.plane;
         const int buf = k & 1;
-        // ---- global loads of this plane (issued before the barrier) ----
-        ld4_or_zero(A.p + pk + 4 * G.plane + row, hd && k + 4 < G.nz, q[7]);
-        ld4_or_zero(A.rho + pk + G.plane + row, hd && k + 1 < G.nz, rq[1]);
-        R hx[4];         // x-halo of p (edge threads)
-        const bool left = (tx == 0), right = (tx == BX - 1);
-        if (left) ld4_or_zero(A.p + pk + (long long)y * G.px + (x0 - 4), y < G.ny && x0 - 4 >= 0, hx);
-        else if (right) ld4_or_zero(A.p + pk + (long long)y * G.px + (x0 + 4), y < G.ny && x0 + 4 < G.px, hx);
-        R hy[4];         // y-halo row of p (rows ty < 7)
-        int hrow = -1;
-        if (DIM == 3 && ty < 7) {
-            const int r = ty;
-            const int yy = r < 3 ? yb - 3 + r : yb + BY + (r - 3);
-            hrow = r < 3 ? r : BY + 3 + (r - 3);
-            ld4_or_zero(A.p + pk + (long long)yy * G.px + x0, yy >= 0 && yy < G.ny && x0 < G.px, hy);
-        }
-        R rhx = R(0);    // rho right of the tile
-        if (right && xb + TW < G.nx && y < G.ny) rhx = A.rho[pk + (long long)y * G.px + xb + TW];
-        R rhy[4];        // rho of the row above the tile
-        if (DIM == 3 && ty == 0)
-            ld4_or_zero(A.rho + pk + (long long)(yb + BY) * G.px + x0, yb + BY < G.ny && x0 < G.px, rhy);
-        uint2 cl = make_uint2(0, 0);
-        if (hd) cl = __ldg(reinterpret_cast<const uint2 *>(A.cls + pk + row));
-        R vv[3][4];
-        R ps[NM][3][4];
-#pragma unroll
-        for (int ax = 0; ax < 3; ++ax) {
-            if (DIM == 2 && ax == 1) continue;
-            if (hd) Io<SS>::ld(A.v[ax] + pk + row, vv[ax]);
-#pragma unroll
-            for (int m = 0; m < NM; ++m)
-                if (hd) Io<SP>::ld(A.psi[m][ax] + pk + row, ps[m][ax]);
-        }
-        // ---- shared-memory tiles of plane k ----
+        unsigned char *st = smem + buf * L::stage;
+        R(*sp)[SW] = reinterpret_cast<R(*)[SW]>(smem + L::o_sp + buf * (size_t)SH * SW * sizeof(R));
+        R(*sr)[TW + 4] = reinterpret_cast<R(*)[TW + 4]>(smem + L::o_sr + buf * (size_t)(BY + 1) * (TW + 4) * sizeof(R));
+        __syncthreads();                           // iteration k-1 is done with stage/tiles (k+1)&1
         {
-            R *dst = &sp[buf][RO + ty][4 + 4 * tx];
+            R *dst = &sp[RO + ty][4 + 4 * tx];
             dst[0] = q[3][0]; dst[1] = q[3][1]; dst[2] = q[3][2]; dst[3] = q[3][3];
-            if (left) { R *h = &sp[buf][RO + ty][0]; h[0] = hx[0]; h[1] = hx[1]; h[2] = hx[2]; h[3] = hx[3]; }
-            if (right) { R *h = &sp[buf][RO + ty][TW + 4]; h[0] = hx[0]; h[1] = hx[1]; h[2] = hx[2]; h[3] = hx[3]; }
-            if (DIM == 3 && hrow >= 0) {
-                R *h = &sp[buf][hrow][4 + 4 * tx];
-                h[0] = hy[0]; h[1] = hy[1]; h[2] = hy[2]; h[3] = hy[3];
-            }
-            R *r = &sr[buf][ty][4 * tx];
+            R *r = &sr[ty][4 * tx];
             r[0] = rq[0][0]; r[1] = rq[0][1]; r[2] = rq[0][2]; r[3] = rq[0][3];
-            if (right) sr[buf][ty][TW] = rhx;
-            if (DIM == 3 && ty == 0) {
-                R *h = &sr[buf][BY][4 * tx];
-                h[0] = rhy[0]; h[1] = rhy[1]; h[2] = rhy[2]; h[3] = rhy[3];
-            }
         }
-        __syncthreads();
+        if (k + 1 < z1) vel_issue<R, SS, SP, DIM, NM, BX, BY>(A, smem, k + 1, x0, y, xb, yb, row, hd);
+        cp_commit();
+        cp_wait<1>();                              // this thread's copies of plane k have landed
+        __syncthreads();                           // ... and everyone's
+        Sm<SS>::ld(reinterpret_cast<const SS *>(st + L::o_pn) + e0, q[7]);
+        Sm<SS>::ld(reinterpret_cast<const SS *>(st + L::o_rn) + e0, rq[1]);
         if (hd) {
-            // ---- derivatives ----
             R g[3][4];
             {
                 R w[12];
-                const R *s = &sp[buf][RO + ty][4 * tx];
+                const R *s = &sp[RO + ty][4 * tx];
 #pragma unroll
                 for (int i = 0; i < 12; ++i) w[i] = s[i];
 #pragma unroll
@@ -290,7 +421,7 @@ k_velocity(const VelArgs<R, SS, SP> A)
                 R c[8][4];
 #pragma unroll
                 for (int r = 0; r < 8; ++r) {
-                    const R *s = &sp[buf][ty + r][4 + 4 * tx];
+                    const R *s = &sp[ty + r][4 + 4 * tx];
                     c[r][0] = s[0]; c[r][1] = s[1]; c[r][2] = s[2]; c[r][3] = s[3];
                 }
 #pragma unroll
@@ -302,54 +433,58 @@ k_velocity(const VelArgs<R, SS, SP> A)
             for (int e = 0; e < 4; ++e)
                 g[2][e] = G.c1 * (q[4][e] - q[3][e]) + G.c2 * (q[5][e] - q[2][e]) +
                           G.c3 * (q[6][e] - q[1][e]) + G.c4 * (q[7][e] - q[0][e]);
-            // ---- face densities -> dt / rho_face ----
             R dtr[3][4];
             {
-                const R *r0 = &sr[buf][ty][4 * tx];
+                const R *r0 = &sr[ty][4 * tx];
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     const R own = r0[e];
                     const R nxr = (x0 + e + 1 < G.nx) ? r0[e + 1] : own;
                     dtr[0][e] = R(2) * G.dt / (own + nxr);
                     if (DIM == 3) {
-                        const R nyr = (y + 1 < G.ny) ? sr[buf][ty + 1][4 * tx + e] : own;
+                        const R nyr = (y + 1 < G.ny) ? sr[ty + 1][4 * tx + e] : own;
                         dtr[1][e] = R(2) * G.dt / (own + nyr);
                     }
                     const R nzr = (k + 1 < G.nz) ? rq[1][e] : own;
                     dtr[2][e] = R(2) * G.dt / (own + nzr);
                 }
             }
+            const uint2 cl = *reinterpret_cast<const uint2 *>(reinterpret_cast<const uint16_t *>(st + L::o_cls) + e0);
             const uint16_t cls4[4] = {(uint16_t)(cl.x & 0xffffu), (uint16_t)(cl.x >> 16),
                                       (uint16_t)(cl.y & 0xffffu), (uint16_t)(cl.y >> 16)};
-            // ---- updates, element by element (class coefficients cached) ----
-            R hdr[4], A1[4], B1[4], H1[4];
-            int cprev = -1;
             const bool pml_x = G.wabs > 0 && (x0 < G.wabs || x0 + 3 >= G.nx - G.wabs);
             const bool pml_y = DIM == 3 && G.wabs > 0 && (y < G.wabs || y >= G.ny - G.wabs);
             const bool pml_z = G.wabs > 0 && (k < G.wabs || k >= G.nz - G.wabs);
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int c = cls4[e];
-                if (c != cprev) {
-                    lut4(A.lut, c, 0, hdr);
-                    lut4(A.lut, c, kLutA1, A1);
-                    lut4(A.lut, c, kLutB1, B1);
-                    lut4(A.lut, c, kLutH1, H1);
-                    cprev = c;
-                }
-                const bool live = x0 + e < G.nx;
+            for (int ax = 0; ax < 3; ++ax) {
+                if (DIM == 2 && ax == 1) continue;
+                R vv[4], ps[NM][4];
+                Sm<SS>::ld(reinterpret_cast<const SS *>(st + L::o_v) + ax * L::TILE + e0, vv);
 #pragma unroll
-                for (int ax = 0; ax < 3; ++ax) {
-                    if (DIM == 2 && ax == 1) continue;
+                for (int m = 0; m < NM; ++m)
+                    Sm<SP>::ld(reinterpret_cast<const SP *>(st + L::o_psi) + (m * 3 + ax) * L::TILE + e0, ps[m]);
+                R hdr[4], A1[4], B1[4], H1[4];
+                int cprev = -1;
+                const bool pml_here = ax == 0 ? pml_x : (ax == 1 ? pml_y : pml_z);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int c = cls4[e];
+                    if (c != cprev) {
+                        lut4(A.lut, c, 0, hdr);
+                        lut4(A.lut, c, kLutA1, A1);
+                        lut4(A.lut, c, kLutB1, B1);
+                        lut4(A.lut, c, kLutH1, H1);
+                        cprev = c;
+                    }
+                    const bool live = x0 + e < G.nx;
                     const R gd = g[ax][e];
-                    R st = gd * hdr[2];
+                    R stv = gd * hdr[2];
 #pragma unroll
                     for (int m = 0; m < NM; ++m) {
-                        const R po = ps[m][ax][e];
-                        st += H1[m] * po;
-                        ps[m][ax][e] = live ? B1[m] * po + A1[m] * gd : R(0);
+                        const R po = ps[m][e];
+                        stv += H1[m] * po;
+                        ps[m][e] = live ? B1[m] * po + A1[m] * gd : R(0);
                     }
-                    const bool pml_here = ax == 0 ? pml_x : (ax == 1 ? pml_y : pml_z);
                     if (pml_here) {
                         const int pos = ax == 0 ? x0 + e : (ax == 1 ? y : k);
                         const R d = A.pd[ax][pos];
@@ -358,22 +493,17 @@ k_velocity(const VelArgs<R, SS, SP> A)
                             pml_ab(d, A.pa[ax][pos], hdr[0], G.dt, a, b);
                             SS *pp = A.psip[ax] + pk + row + e;
                             const R po = Io<SS>::ld1(pp);
-                            st += R(0.5) * (R(1) + b) * po + R(0.5) * a * gd;
+                            stv += R(0.5) * (R(1) + b) * po + R(0.5) * a * gd;
                             Io<SS>::st1(pp, SS(b * po + a * gd));
                         }
                     }
-                    vv[ax][e] = live ? vv[ax][e] - dtr[ax][e] * st : R(0);
+                    vv[e] = live ? vv[e] - dtr[ax][e] * stv : R(0);
                 }
-            }
+                Io<SS>::st(A.v[ax] + pk + row, vv);
 #pragma unroll
-            for (int ax = 0; ax < 3; ++ax) {
-                if (DIM == 2 && ax == 1) continue;
-                Io<SS>::st(A.v[ax] + pk + row, vv[ax]);
-#pragma unroll
-                for (int m = 0; m < NM; ++m) Io<SP>::st(A.psi[m][ax] + pk + row, ps[m][ax]);
+                for (int m = 0; m < NM; ++m) Io<SP>::st(A.psi[m][ax] + pk + row, ps[m]);
             }
         }
-        // ---- advance the queues ----
 #pragma unroll
         for (int j = 0; j < 7; ++j)
 #pragma unroll
@@ -381,20 +511,66 @@ k_velocity(const VelArgs<R, SS, SP> A)
 #pragma unroll
         for (int e = 0; e < 4; ++e) rq[0][e] = rq[1][e];
     }
+    cp_wait<0>();
 }
 
 // ---------------------------------------------------------------------------
 // pressure sweep
 
 template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY, bool NL>
-__global__ void __launch_bounds__(BX *BY)
+__device__ __forceinline__ void pres_issue(const PresArgs<R, SS, SP> &A, unsigned char *sm, int k, int x0, int y,
+                                           int yb, long long row, bool hd)
+{
+    using L = PresSmem<R, SS, SP, DIM, NM, BX, BY>;
+    const Geo<R> &G = A.g;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const long long pk = (long long)k * G.plane;
+    unsigned char *st = sm + (k & 1) * L::stage;
+    const int e0 = ty * L::TW + 4 * tx;
+    const SS *gz = A.p;
+    {
+        const bool ok = hd && k + 3 < G.nz;
+        cp_async4(reinterpret_cast<SS *>(st + L::o_qn) + e0, ok ? A.v[2] + pk + 3 * G.plane + row : gz, ok);
+    }
+    cp_async4(reinterpret_cast<SS *>(st + L::o_p) + e0, hd ? A.p + pk + row : gz, hd);
+    cp_async4(reinterpret_cast<SS *>(st + L::o_kd) + e0, hd ? A.kdt + pk + row : gz, hd);
+    if (NL) cp_async4(reinterpret_cast<SS *>(st + L::o_bd) + e0, hd ? A.b2dt + pk + row : gz, hd);
+#pragma unroll
+    for (int m = 0; m < NM; ++m)
+        cp_async4(reinterpret_cast<SP *>(st + L::o_psi) + m * L::TILE + e0,
+                  hd ? A.psi[m] + pk + row : reinterpret_cast<const SP *>(gz), hd);
+    cp_async<8>(reinterpret_cast<uint16_t *>(st + L::o_cls) + e0, hd ? (const void *)(A.cls + pk + row) : (const void *)gz, hd);
+    // v_x (with x halo) and v_y (with y halo) of plane k straight into the tiles
+    R *svx = reinterpret_cast<R *>(sm + L::o_svx) + (k & 1) * BY * L::SWX;
+    cp_async4(reinterpret_cast<SS *>(svx + ty * L::SWX + 4 + 4 * tx), hd ? A.v[0] + pk + row : gz, hd);
+    if (tx == 0) {
+        const bool ok = y < G.ny && x0 - 4 >= 0;
+        cp_async4(reinterpret_cast<SS *>(svx + ty * L::SWX), ok ? A.v[0] + pk + (long long)y * G.px + (x0 - 4) : gz, ok);
+    }
+    if (tx == BX - 1) {
+        const bool ok = y < G.ny && x0 + 4 < G.px;
+        cp_async4(reinterpret_cast<SS *>(svx + ty * L::SWX + L::TW + 4), ok ? A.v[0] + pk + (long long)y * G.px + (x0 + 4) : gz, ok);
+    }
+    if (DIM == 3) {
+        R *svy = reinterpret_cast<R *>(sm + L::o_svy) + (k & 1) * L::SHY * L::TW;
+        cp_async4(reinterpret_cast<SS *>(svy + (4 + ty) * L::TW + 4 * tx), hd ? A.v[1] + pk + row : gz, hd);
+        if (ty < 7) {
+            const int yy = ty < 4 ? yb - 4 + ty : yb + BY + (ty - 4);
+            const int hrow = ty < 4 ? ty : BY + 4 + (ty - 4);
+            const bool ok = yy >= 0 && yy < G.ny && x0 < G.px;
+            cp_async4(reinterpret_cast<SS *>(svy + hrow * L::TW + 4 * tx), ok ? A.v[1] + pk + (long long)yy * G.px + x0 : gz, ok);
+        }
+    }
+}
+
+template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY, bool NL>
+__global__ void __launch_bounds__(BX *BY, 1)
 k_pressure(const PresArgs<R, SS, SP> A)
 {
-    constexpr int TW = 4 * BX;
-    constexpr int SWX = TW + 8;                  // vx row with 4 halo columns each side
-    constexpr int SHY = DIM == 3 ? BY + 7 : 1;   // vy rows: 4 below, 3 above
-    __shared__ __align__(16) R svx[2][BY][SWX];
-    __shared__ __align__(16) R svy[2][SHY][TW];
+    using L = PresSmem<R, SS, SP, DIM, NM, BX, BY>;
+    constexpr int TW = L::TW, SWX = L::SWX, SHY = L::SHY;
+    static_assert(DIM == 2 || BY >= 7, "the y halo needs 7 thread rows");
+    extern __shared__ __align__(128) unsigned char smem[];
 
     const Geo<R> &G = A.g;
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -404,6 +580,7 @@ k_pressure(const PresArgs<R, SS, SP> A)
     const int z1 = min(G.nz, z0 + G.zseg);
     const bool hd = (x0 < G.nx) && (y < G.ny);
     const long long row = (long long)y * G.px + x0;
+    const int e0 = ty * TW + 4 * tx;
 
     R qz[8][4];     // vz of own columns, planes k-4 .. k+3
 #pragma unroll
@@ -413,55 +590,25 @@ k_pressure(const PresArgs<R, SS, SP> A)
     }
     R pmax = R(0);
     bool bad = false;
-
+    if (z0 < z1) pres_issue<R, SS, SP, DIM, NM, BX, BY, NL>(A, smem, z0, x0, y, yb, row, hd);
+    cp_commit();
     for (int k = z0; k < z1; ++k) {
         const long long pk = (long long)k * G.plane;
         const int buf = k & 1;
-        ld4_or_zero(A.v[2] + pk + 3 * G.plane + row, hd && k + 3 < G.nz, qz[7]);
-        R cx[4], hx[4];
-        ld4_or_zero(A.v[0] + pk + row, hd, cx);
-        const bool left = (tx == 0), right = (tx == BX - 1);
-        if (left) ld4_or_zero(A.v[0] + pk + (long long)y * G.px + (x0 - 4), y < G.ny && x0 - 4 >= 0, hx);
-        else if (right) ld4_or_zero(A.v[0] + pk + (long long)y * G.px + (x0 + 4), y < G.ny && x0 + 4 < G.px, hx);
-        R cy[4], hy[4];
-        int hrow = -1;
-        if (DIM == 3) {
-            ld4_or_zero(A.v[1] + pk + row, hd, cy);
-            if (ty < 7) {
-                const int r = ty;
-                const int yy = r < 4 ? yb - 4 + r : yb + BY + (r - 4);
-                hrow = r < 4 ? r : BY + 4 + (r - 4);
-                ld4_or_zero(A.v[1] + pk + (long long)yy * G.px + x0, yy >= 0 && yy < G.ny && x0 < G.px, hy);
-            }
-        }
-        R pv[4], kd[4], bd[4];
-        R ps[NM][4];
-        uint2 cl = make_uint2(0, 0);
-        if (hd) {
-            Io<SS>::ld(A.p + pk + row, pv);
-            Io<SS>::ldg(A.kdt + pk + row, kd);
-            if (NL) Io<SS>::ldg(A.b2dt + pk + row, bd);
-            cl = __ldg(reinterpret_cast<const uint2 *>(A.cls + pk + row));
-#pragma unroll
-            for (int m = 0; m < NM; ++m) Io<SP>::ld(A.psi[m] + pk + row, ps[m]);
-        }
-        {
-            R *d = &svx[buf][ty][4 + 4 * tx];
-            d[0] = cx[0]; d[1] = cx[1]; d[2] = cx[2]; d[3] = cx[3];
-            if (left) { R *h = &svx[buf][ty][0]; h[0] = hx[0]; h[1] = hx[1]; h[2] = hx[2]; h[3] = hx[3]; }
-            if (right) { R *h = &svx[buf][ty][TW + 4]; h[0] = hx[0]; h[1] = hx[1]; h[2] = hx[2]; h[3] = hx[3]; }
-            if (DIM == 3) {
-                R *c = &svy[buf][4 + ty][4 * tx];
-                c[0] = cy[0]; c[1] = cy[1]; c[2] = cy[2]; c[3] = cy[3];
-                if (hrow >= 0) { R *h = &svy[buf][hrow][4 * tx]; h[0] = hy[0]; h[1] = hy[1]; h[2] = hy[2]; h[3] = hy[3]; }
-            }
-        }
+        unsigned char *st = smem + buf * L::stage;
+        const R(*svx)[SWX] = reinterpret_cast<const R(*)[SWX]>(smem + L::o_svx + buf * (size_t)BY * SWX * sizeof(R));
+        const R(*svy)[TW] = reinterpret_cast<const R(*)[TW]>(smem + L::o_svy + buf * (size_t)SHY * TW * sizeof(R));
         __syncthreads();
+        if (k + 1 < z1) pres_issue<R, SS, SP, DIM, NM, BX, BY, NL>(A, smem, k + 1, x0, y, yb, row, hd);
+        cp_commit();
+        cp_wait<1>();
+        __syncthreads();
+        Sm<SS>::ld(reinterpret_cast<const SS *>(st + L::o_qn) + e0, qz[7]);
         if (hd) {
             R qd[3][4];
             {
                 R w[12];
-                const R *s = &svx[buf][ty][4 * tx];
+                const R *s = &svx[ty][4 * tx];
 #pragma unroll
                 for (int i = 0; i < 12; ++i) w[i] = s[i];
 #pragma unroll
@@ -473,7 +620,7 @@ k_pressure(const PresArgs<R, SS, SP> A)
                 R c[8][4];
 #pragma unroll
                 for (int r = 0; r < 8; ++r) {
-                    const R *s = &svy[buf][ty + r][4 * tx];
+                    const R *s = &svy[ty + r][4 * tx];
                     c[r][0] = s[0]; c[r][1] = s[1]; c[r][2] = s[2]; c[r][3] = s[3];
                 }
 #pragma unroll
@@ -485,6 +632,13 @@ k_pressure(const PresArgs<R, SS, SP> A)
             for (int e = 0; e < 4; ++e)
                 qd[2][e] = G.c1 * (qz[4][e] - qz[3][e]) + G.c2 * (qz[5][e] - qz[2][e]) +
                            G.c3 * (qz[6][e] - qz[1][e]) + G.c4 * (qz[7][e] - qz[0][e]);
+            R pv[4], kd[4], bd[4], ps[NM][4];
+            Sm<SS>::ld(reinterpret_cast<const SS *>(st + L::o_p) + e0, pv);
+            Sm<SS>::ld(reinterpret_cast<const SS *>(st + L::o_kd) + e0, kd);
+            if (NL) Sm<SS>::ld(reinterpret_cast<const SS *>(st + L::o_bd) + e0, bd);
+#pragma unroll
+            for (int m = 0; m < NM; ++m) Sm<SP>::ld(reinterpret_cast<const SP *>(st + L::o_psi) + m * L::TILE + e0, ps[m]);
+            const uint2 cl = *reinterpret_cast<const uint2 *>(reinterpret_cast<const uint16_t *>(st + L::o_cls) + e0);
             const uint16_t cls4[4] = {(uint16_t)(cl.x & 0xffffu), (uint16_t)(cl.x >> 16),
                                       (uint16_t)(cl.y & 0xffffu), (uint16_t)(cl.y >> 16)};
             R hdr[4], A2[4], B2[4], H2[4];
@@ -505,11 +659,11 @@ k_pressure(const PresArgs<R, SS, SP> A)
                 const bool live = x0 + e < G.nx;
                 R div = qd[0][e] + qd[2][e];
                 if (DIM == 3) div += qd[1][e];
-                R st = div * hdr[3];
+                R stp = div * hdr[3];
 #pragma unroll
                 for (int m = 0; m < NM; ++m) {
                     const R po = ps[m][e];
-                    st += H2[m] * po;
+                    stp += H2[m] * po;
                     ps[m][e] = live ? B2[m] * po + A2[m] * div : R(0);
                 }
 #pragma unroll
@@ -524,13 +678,13 @@ k_pressure(const PresArgs<R, SS, SP> A)
                         pml_ab(d, A.pa[ax][pos], hdr[1], G.dt, a, b);
                         SS *pp = A.psip[ax] + pk + row + e;
                         const R po = Io<SS>::ld1(pp);
-                        st += R(0.5) * (R(1) + b) * po + R(0.5) * a * qd[ax][e];
+                        stp += R(0.5) * (R(1) + b) * po + R(0.5) * a * qd[ax][e];
                         Io<SS>::st1(pp, SS(b * po + a * qd[ax][e]));
                     }
                 }
                 R fac = kd[e];
                 if (NL) fac += bd[e] * pv[e];
-                const R pn = live ? pv[e] - fac * st : R(0);
+                const R pn = live ? pv[e] - fac * stp : R(0);
                 pv[e] = pn;
                 const R ap = fabs(pn);
                 bad |= !(ap <= R(3.0e38));
@@ -545,6 +699,7 @@ k_pressure(const PresArgs<R, SS, SP> A)
 #pragma unroll
             for (int e = 0; e < 4; ++e) qz[j][e] = qz[j + 1][e];
     }
+    cp_wait<0>();
     // ---- stability monitor: one atomic per warp ----
     float m = bad ? 0.0f : (float)fmin(pmax, R(3.0e38));
     unsigned any_bad = __ballot_sync(0xffffffffu, bad);

@@ -30,12 +30,27 @@ template <typename R> Geo<R> make_geo(const fw_medium *m)
     return g;
 }
 
-// which: bit 0 = velocity sweep, bit 1 = pressure sweep
+// which: bit 0 = velocity sweep, bit 1 = pressure sweep, bit 2 = only opt the
+// instances into their dynamic shared memory (done once at medium creation,
+// outside any stream capture)
 template <typename R, typename SS, typename SP, int DIM, int NM>
 cudaError_t launch_dn(const fw_medium *m, cudaStream_t s, int which)
 {
     constexpr int BX = DIM == 3 ? Tile3<R>::BX : Tile2<R>::BX;
     constexpr int BY = DIM == 3 ? Tile3<R>::BY : Tile2<R>::BY;
+    using LV = VelSmem<R, SS, SP, DIM, NM, BX, BY>;
+    using LP = PresSmem<R, SS, SP, DIM, NM, BX, BY>;
+    if (which & 4) {
+        cudaError_t e = cudaFuncSetAttribute(k_velocity<R, SS, SP, DIM, NM, BX, BY>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LV::bytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_pressure<R, SS, SP, DIM, NM, BX, BY, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LP::bytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_pressure<R, SS, SP, DIM, NM, BX, BY, false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LP::bytes);
+        return e;
+    }
     const Geo<R> g = make_geo<R>(m);
     dim3 block(BX, BY);
     dim3 grid((m->NX + 4 * BX - 1) / (4 * BX), (m->NY + BY - 1) / BY, (m->NZ + m->zseg - 1) / m->zseg);
@@ -53,7 +68,7 @@ cudaError_t launch_dn(const fw_medium *m, cudaStream_t s, int which)
     va.rho = static_cast<const SS *>(m->rho);
     va.cls = m->cls;
     va.lut = static_cast<const R *>(m->lut);
-    if (which & 1) k_velocity<R, SS, SP, DIM, NM, BX, BY><<<grid, block, 0, s>>>(va);
+    if (which & 1) k_velocity<R, SS, SP, DIM, NM, BX, BY><<<grid, block, LV::bytes, s>>>(va);
     if (!(which & 2)) return cudaGetLastError();
 
     PresArgs<R, SS, SP> pa{};
@@ -72,9 +87,9 @@ cudaError_t launch_dn(const fw_medium *m, cudaStream_t s, int which)
     pa.lut = static_cast<const R *>(m->lut);
     pa.mon = m->mon;
     if (m->nonlinear)
-        k_pressure<R, SS, SP, DIM, NM, BX, BY, true><<<grid, block, 0, s>>>(pa);
+        k_pressure<R, SS, SP, DIM, NM, BX, BY, true><<<grid, block, LP::bytes, s>>>(pa);
     else
-        k_pressure<R, SS, SP, DIM, NM, BX, BY, false><<<grid, block, 0, s>>>(pa);
+        k_pressure<R, SS, SP, DIM, NM, BX, BY, false><<<grid, block, LP::bytes, s>>>(pa);
     return cudaGetLastError();
 }
 
