@@ -225,10 +225,11 @@ int fw_run(fw_medium *m, int n_steps, void *stream);
 /* fw_step with a CUDA event around each sweep: advances n_steps on stream
  * (plain launches), waits for them, and returns the summed device time [ms]
  * of the velocity sweeps, the pressure sweeps and the source/receiver
- * kernels, and the number of kernels launched.  Output pointers may be
- * NULL.  For measurement; results equal fw_step's. */
+ * kernels, the device time from the first launch to the last, and the number
+ * of kernels launched.  Output pointers may be NULL.  For measurement;
+ * results equal fw_step's. */
 int fw_step_timed(fw_medium *m, int n_steps, void *stream, double *ms_velocity, double *ms_pressure,
-                  double *ms_io, int *n_launches);
+                  double *ms_io, double *ms_total, int *n_launches);
 
 /* Replace waveform samples [it0, it0+n) of every waveform row from samples
  * (n_wave x n floats, host or device; pinned host memory keeps the copy

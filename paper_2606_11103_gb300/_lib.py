@@ -81,7 +81,7 @@ SIGNATURES = {
     "fw_set_receivers": (_I, [_P, _P, _I, _I]),
     "fw_step": (_I, [_P, _I, _P]),
     "fw_run": (_I, [_P, _I, _P]),
-    "fw_step_timed": (_I, [_P, _I, _P, _D, _D, _D, C.POINTER(_I)]),
+    "fw_step_timed": (_I, [_P, _I, _P, _D, _D, _D, _D, C.POINTER(_I)]),
     "fw_set_waveform_samples": (_I, [_P, _I, _I, _P, _P]),
     "fw_read_receivers_range": (_I, [_P, _I, _I, _P, _P]),
     "fw_read_field": (_I, [_P, _I, _I, _P, _I, _P]),

@@ -56,7 +56,9 @@ def _compile(src, nvcc, extra):
 
 
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    """Compile and link the library; returns its path."""
+    """Compile and link the library; returns its path.  FWGB_NVCC_EXTRA (env)
+    adds nvcc flags, e.g. tile-shape tuning macros."""
+    extra = list(extra) + os.environ.get("FWGB_NVCC_EXTRA", "").split()
     if not force and up_to_date():
         return LIB
     nvcc = _nvcc()

@@ -503,12 +503,14 @@ int choose_zseg(const fw_medium *m)
         int z = std::atoi(e);
         if (z >= 8 && z <= 1024) return z;
     }
-    // enough CTAs for several waves over 152 SMs, at least 16 planes per CTA
+    // 16 planes per CTA measured best on the 512^3 workload (L2 sharing of
+    // the halo planes between concurrently resident CTAs); at least 8 waves
+    // of CTAs over the 152 SMs
     const int tw = m->ndim == 3 ? (m->es == 8 ? 64 : 128) : 256;
     const int by = m->ndim == 3 ? 8 : 1;
     long long tiles = (long long)((m->NX + tw - 1) / tw) * ((m->NY + by - 1) / by);
-    int z = 64;
-    while (z > 16 && tiles * ((m->NZ + z - 1) / z) < 152LL * 8) z /= 2;
+    int z = 16;
+    while (z > 8 && tiles * ((m->NZ + z - 1) / z) < 152LL * 8) z /= 2;
     return z;
 }
 
@@ -910,12 +912,14 @@ int fw_run(fw_medium *m, int n_steps, void *stream)
 }
 
 int fw_step_timed(fw_medium *m, int n_steps, void *stream, double *ms_velocity, double *ms_pressure,
-                  double *ms_io, int *n_launches)
+                  double *ms_io, double *ms_total, int *n_launches)
 {
     if (!m || n_steps < 0) return FW_ERR_ARG;
     if (m->sticky) return m->sticky;
     cudaStream_t s = (cudaStream_t)stream;
-    std::vector<cudaEvent_t> ev(3 * (size_t)n_steps + 1);
+    // all events exist before the first is recorded, so host-side creation
+    // never shows up as device time
+    std::vector<cudaEvent_t> ev(3 * (size_t)n_steps + 1, nullptr);
     for (auto &e : ev)
         if (cudaEventCreate(&e) != cudaSuccess) {
             for (auto &x : ev) if (x) cudaEventDestroy(x);
@@ -938,6 +942,7 @@ int fw_step_timed(fw_medium *m, int n_steps, void *stream, double *ms_velocity, 
             rc = FW_ERR_CUDA;
     }
     double tv = 0, tp = 0, ti = 0;
+    float tot = 0;
     for (int j = 0; j < n_steps && rc == FW_OK; ++j) {
         float a = 0, b = 0, c = 0;
         cudaEventElapsedTime(&a, ev[3 * j], ev[3 * j + 1]);
@@ -945,11 +950,13 @@ int fw_step_timed(fw_medium *m, int n_steps, void *stream, double *ms_velocity, 
         cudaEventElapsedTime(&c, ev[3 * j + 2], ev[3 * j + 3]);
         tv += a; tp += b; ti += c;
     }
+    if (rc == FW_OK && n_steps > 0) cudaEventElapsedTime(&tot, ev[0], ev[3 * (size_t)n_steps]);
     for (auto &e : ev) cudaEventDestroy(e);
     if (rc) return rc;
     if (ms_velocity) *ms_velocity = tv;
     if (ms_pressure) *ms_pressure = tp;
     if (ms_io) *ms_io = ti;
+    if (ms_total) *ms_total = tot;
     if (n_launches) *n_launches = launches;
     m->step += n_steps;
     m->last_stream = s;

@@ -130,6 +130,8 @@ template <> __device__ __forceinline__ void lut4<double>(const double *lut, int 
 }
 
 __device__ __forceinline__ float fw_exp(float x) { return expf(x); }
+__device__ __forceinline__ float fw_rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double fw_rcp(double x) { return 1.0 / x; }
 __device__ __forceinline__ double fw_exp(double x) { return exp(x); }
 
 // Absorbing-layer mechanism coefficients (Eqs. relaxation_a/b with the
@@ -276,7 +278,8 @@ template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY>
     static constexpr size_t o_pn = o_psi + (size_t)NM * 3 * TILE * sizeof(SP);
     static constexpr size_t o_rn = o_pn + TILE * sizeof(SS);
     static constexpr size_t o_cls = o_rn + TILE * sizeof(SS);
-    static constexpr size_t stage = (o_cls + TILE * 2 + 127) / 128 * 128;
+    static constexpr size_t o_pml = o_cls + (TILE * 2 + 15) / 16 * 16;     // absorbing-layer psi per axis
+    static constexpr size_t stage = (o_pml + 3 * TILE * sizeof(SS) + 127) / 128 * 128;
     // derivative tiles
     static constexpr size_t o_sp = 2 * stage;
     static constexpr size_t o_sr = o_sp + 2 * (size_t)SH * SW * sizeof(R);
@@ -292,7 +295,8 @@ template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY>
     static constexpr size_t o_bd = o_kd + TILE * sizeof(SS);
     static constexpr size_t o_psi = o_bd + TILE * sizeof(SS);
     static constexpr size_t o_cls = o_psi + (size_t)NM * TILE * sizeof(SP);
-    static constexpr size_t stage = (o_cls + TILE * 2 + 127) / 128 * 128;
+    static constexpr size_t o_pml = o_cls + (TILE * 2 + 15) / 16 * 16;
+    static constexpr size_t stage = (o_pml + 3 * TILE * sizeof(SS) + 127) / 128 * 128;
     static constexpr size_t o_svx = 2 * stage;
     static constexpr size_t o_svy = o_svx + 2 * (size_t)BY * SWX * sizeof(R);
     static constexpr size_t bytes = o_svy + 2 * (size_t)SHY * TW * sizeof(R);
@@ -328,6 +332,13 @@ __device__ __forceinline__ void vel_issue(const VelArgs<R, SS, SP> &A, unsigned 
         cp_async4(reinterpret_cast<SS *>(st + L::o_rn) + e0, okr ? A.rho + pk + G.plane + row : gz, okr);
         cp_async<8>(reinterpret_cast<uint16_t *>(st + L::o_cls) + e0, hd ? (const void *)(A.cls + pk + row) : (const void *)gz, hd);
     }
+    if (G.wabs > 0 && hd) {                   // absorbing-layer memory where this thread needs it
+        const bool in[3] = {x0 < G.wabs || x0 + 3 >= G.nx - G.wabs, DIM == 3 && (y < G.wabs || y >= G.ny - G.wabs),
+                            k < G.wabs || k >= G.nz - G.wabs};
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax)
+            if (in[ax]) cp_async4(reinterpret_cast<SS *>(st + L::o_pml) + ax * L::TILE + e0, A.psip[ax] + pk + row, true);
+    }
     // halos of plane k straight into the derivative tiles of parity k&1
     R *sp = reinterpret_cast<R *>(sm + L::o_sp) + (k & 1) * L::SH * L::SW;
     R *sr = reinterpret_cast<R *>(sm + L::o_sr) + (k & 1) * (BY + 1) * (L::TW + 4);
@@ -343,11 +354,13 @@ __device__ __forceinline__ void vel_issue(const VelArgs<R, SS, SP> &A, unsigned 
         cp_async<sizeof(SS)>(reinterpret_cast<SS *>(sr + ty * (L::TW + 4) + L::TW),
                              okr ? A.rho + pk + (long long)y * G.px + xb + L::TW : gz, okr);
     }
-    if (DIM == 3 && ty < 7) {
-        const int yy = ty < 3 ? yb - 3 + ty : yb + BY + (ty - 3);
-        const int hrow = ty < 3 ? ty : BY + 3 + (ty - 3);
-        const bool ok = yy >= 0 && yy < G.ny && x0 < G.px;
-        cp_async4(reinterpret_cast<SS *>(sp + hrow * L::SW + 4 + 4 * tx), ok ? A.p + pk + (long long)yy * G.px + x0 : gz, ok);
+    if (DIM == 3) {
+        for (int r = ty; r < 7; r += BY) {      // 3 halo rows below the tile, 4 above
+            const int yy = r < 3 ? yb - 3 + r : yb + BY + (r - 3);
+            const int hrow = r < 3 ? r : BY + 3 + (r - 3);
+            const bool ok = yy >= 0 && yy < G.ny && x0 < G.px;
+            cp_async4(reinterpret_cast<SS *>(sp + hrow * L::SW + 4 + 4 * tx), ok ? A.p + pk + (long long)yy * G.px + x0 : gz, ok);
+        }
     }
     if (DIM == 3 && ty == 0) {
         const bool ok = yb + BY < G.ny && x0 < G.px;
@@ -356,12 +369,11 @@ __device__ __forceinline__ void vel_issue(const VelArgs<R, SS, SP> &A, unsigned 
 }
 
 template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY>
-__global__ void __launch_bounds__(BX *BY, 1)
+__global__ void __launch_bounds__(BX *BY, (DIM == 3 && BY < 8) ? 2 : 1)
 k_velocity(const VelArgs<R, SS, SP> A)
 {
     using L = VelSmem<R, SS, SP, DIM, NM, BX, BY>;
     constexpr int TW = L::TW, SW = L::SW, SH = L::SH, RO = L::RO;
-    static_assert(DIM == 2 || BY >= 7, "the y halo needs 7 thread rows");
     static_assert(sizeof(SS) == sizeof(R), "state is stored in the arithmetic type");
     extern __shared__ __align__(128) unsigned char smem[];
 
@@ -385,6 +397,17 @@ k_velocity(const VelArgs<R, SS, SP> A)
     ld4_or_zero(A.rho + z0 * G.plane + row, hd && z0 < G.nz, rq[0]);
     if (z0 < z1) vel_issue<R, SS, SP, DIM, NM, BX, BY>(A, smem, z0, x0, y, xb, yb, row, hd);
     cp_commit();
+    // absorbing-layer profile of this thread's x and y positions (fixed over the march)
+    const bool pml_x = G.wabs > 0 && (x0 < G.wabs || x0 + 3 >= G.nx - G.wabs);
+    const bool pml_y = DIM == 3 && G.wabs > 0 && (y < G.wabs || y >= G.ny - G.wabs);
+    R pdx[4] = {0, 0, 0, 0}, pax[4] = {0, 0, 0, 0}, pdy = 0, pay = 0;
+    if (pml_x && hd)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) { pdx[e] = A.pd[0][x0 + e]; pax[e] = A.pa[0][x0 + e]; }
+    if (pml_y && hd) { pdy = A.pd[1][y]; pay = A.pa[1][y]; }
+    // class coefficients of the last class seen (classes rarely change along a column)
+    int ccls = -1;
+    R hdr[4], A1[4], B1[4], H1[4];
 
     for (int k = z0; k < z1; ++k) {
         const long long pk = (long long)k * G.plane;
@@ -401,6 +424,9 @@ k_velocity(const VelArgs<R, SS, SP> A)
         }
         if (k + 1 < z1) vel_issue<R, SS, SP, DIM, NM, BX, BY>(A, smem, k + 1, x0, y, xb, yb, row, hd);
         cp_commit();
+        const bool pml_z = G.wabs > 0 && (k < G.wabs || k >= G.nz - G.wabs);
+        R pdz = 0, paz = 0;
+        if (pml_z) { pdz = A.pd[2][k]; paz = A.pa[2][k]; }
         cp_wait<1>();                              // this thread's copies of plane k have landed
         __syncthreads();                           // ... and everyone's
         Sm<SS>::ld(reinterpret_cast<const SS *>(st + L::o_pn) + e0, q[7]);
@@ -440,21 +466,19 @@ k_velocity(const VelArgs<R, SS, SP> A)
                 for (int e = 0; e < 4; ++e) {
                     const R own = r0[e];
                     const R nxr = (x0 + e + 1 < G.nx) ? r0[e + 1] : own;
-                    dtr[0][e] = R(2) * G.dt / (own + nxr);
+                    dtr[0][e] = R(2) * G.dt * fw_rcp(own + nxr);
                     if (DIM == 3) {
                         const R nyr = (y + 1 < G.ny) ? sr[ty + 1][4 * tx + e] : own;
-                        dtr[1][e] = R(2) * G.dt / (own + nyr);
+                        dtr[1][e] = R(2) * G.dt * fw_rcp(own + nyr);
                     }
                     const R nzr = (k + 1 < G.nz) ? rq[1][e] : own;
-                    dtr[2][e] = R(2) * G.dt / (own + nzr);
+                    dtr[2][e] = R(2) * G.dt * fw_rcp(own + nzr);
                 }
             }
             const uint2 cl = *reinterpret_cast<const uint2 *>(reinterpret_cast<const uint16_t *>(st + L::o_cls) + e0);
             const uint16_t cls4[4] = {(uint16_t)(cl.x & 0xffffu), (uint16_t)(cl.x >> 16),
                                       (uint16_t)(cl.y & 0xffffu), (uint16_t)(cl.y >> 16)};
-            const bool pml_x = G.wabs > 0 && (x0 < G.wabs || x0 + 3 >= G.nx - G.wabs);
-            const bool pml_y = DIM == 3 && G.wabs > 0 && (y < G.wabs || y >= G.ny - G.wabs);
-            const bool pml_z = G.wabs > 0 && (k < G.wabs || k >= G.nz - G.wabs);
+            // one direction at a time: its v and psi come from the stage
 #pragma unroll
             for (int ax = 0; ax < 3; ++ax) {
                 if (DIM == 2 && ax == 1) continue;
@@ -463,18 +487,18 @@ k_velocity(const VelArgs<R, SS, SP> A)
 #pragma unroll
                 for (int m = 0; m < NM; ++m)
                     Sm<SP>::ld(reinterpret_cast<const SP *>(st + L::o_psi) + (m * 3 + ax) * L::TILE + e0, ps[m]);
-                R hdr[4], A1[4], B1[4], H1[4];
-                int cprev = -1;
                 const bool pml_here = ax == 0 ? pml_x : (ax == 1 ? pml_y : pml_z);
+                R pp[4];
+                if (pml_here) Sm<SS>::ld(reinterpret_cast<const SS *>(st + L::o_pml) + ax * L::TILE + e0, pp);
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     const int c = cls4[e];
-                    if (c != cprev) {
+                    if (c != ccls) {
                         lut4(A.lut, c, 0, hdr);
                         lut4(A.lut, c, kLutA1, A1);
                         lut4(A.lut, c, kLutB1, B1);
                         lut4(A.lut, c, kLutH1, H1);
-                        cprev = c;
+                        ccls = c;
                     }
                     const bool live = x0 + e < G.nx;
                     const R gd = g[ax][e];
@@ -486,15 +510,13 @@ k_velocity(const VelArgs<R, SS, SP> A)
                         ps[m][e] = live ? B1[m] * po + A1[m] * gd : R(0);
                     }
                     if (pml_here) {
-                        const int pos = ax == 0 ? x0 + e : (ax == 1 ? y : k);
-                        const R d = A.pd[ax][pos];
+                        const R d = ax == 0 ? pdx[e] : (ax == 1 ? pdy : pdz);
                         if (d > R(0) && live) {
                             R a, b;
-                            pml_ab(d, A.pa[ax][pos], hdr[0], G.dt, a, b);
-                            SS *pp = A.psip[ax] + pk + row + e;
-                            const R po = Io<SS>::ld1(pp);
+                            pml_ab(d, ax == 0 ? pax[e] : (ax == 1 ? pay : paz), hdr[0], G.dt, a, b);
+                            const R po = pp[e];
                             stv += R(0.5) * (R(1) + b) * po + R(0.5) * a * gd;
-                            Io<SS>::st1(pp, SS(b * po + a * gd));
+                            pp[e] = b * po + a * gd;
                         }
                     }
                     vv[e] = live ? vv[e] - dtr[ax][e] * stv : R(0);
@@ -502,6 +524,7 @@ k_velocity(const VelArgs<R, SS, SP> A)
                 Io<SS>::st(A.v[ax] + pk + row, vv);
 #pragma unroll
                 for (int m = 0; m < NM; ++m) Io<SP>::st(A.psi[m][ax] + pk + row, ps[m]);
+                if (pml_here) Io<SS>::st(A.psip[ax] + pk + row, pp);
             }
         }
 #pragma unroll
@@ -540,6 +563,13 @@ __device__ __forceinline__ void pres_issue(const PresArgs<R, SS, SP> &A, unsigne
         cp_async4(reinterpret_cast<SP *>(st + L::o_psi) + m * L::TILE + e0,
                   hd ? A.psi[m] + pk + row : reinterpret_cast<const SP *>(gz), hd);
     cp_async<8>(reinterpret_cast<uint16_t *>(st + L::o_cls) + e0, hd ? (const void *)(A.cls + pk + row) : (const void *)gz, hd);
+    if (G.wabs > 0 && hd) {
+        const bool in[3] = {x0 < G.wabs || x0 + 3 >= G.nx - G.wabs, DIM == 3 && (y < G.wabs || y >= G.ny - G.wabs),
+                            k < G.wabs || k >= G.nz - G.wabs};
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax)
+            if (in[ax]) cp_async4(reinterpret_cast<SS *>(st + L::o_pml) + ax * L::TILE + e0, A.psip[ax] + pk + row, true);
+    }
     // v_x (with x halo) and v_y (with y halo) of plane k straight into the tiles
     R *svx = reinterpret_cast<R *>(sm + L::o_svx) + (k & 1) * BY * L::SWX;
     cp_async4(reinterpret_cast<SS *>(svx + ty * L::SWX + 4 + 4 * tx), hd ? A.v[0] + pk + row : gz, hd);
@@ -554,9 +584,9 @@ __device__ __forceinline__ void pres_issue(const PresArgs<R, SS, SP> &A, unsigne
     if (DIM == 3) {
         R *svy = reinterpret_cast<R *>(sm + L::o_svy) + (k & 1) * L::SHY * L::TW;
         cp_async4(reinterpret_cast<SS *>(svy + (4 + ty) * L::TW + 4 * tx), hd ? A.v[1] + pk + row : gz, hd);
-        if (ty < 7) {
-            const int yy = ty < 4 ? yb - 4 + ty : yb + BY + (ty - 4);
-            const int hrow = ty < 4 ? ty : BY + 4 + (ty - 4);
+        for (int r = ty; r < 7; r += BY) {      // 4 halo rows below the tile, 3 above
+            const int yy = r < 4 ? yb - 4 + r : yb + BY + (r - 4);
+            const int hrow = r < 4 ? r : BY + 4 + (r - 4);
             const bool ok = yy >= 0 && yy < G.ny && x0 < G.px;
             cp_async4(reinterpret_cast<SS *>(svy + hrow * L::TW + 4 * tx), ok ? A.v[1] + pk + (long long)yy * G.px + x0 : gz, ok);
         }
@@ -564,12 +594,11 @@ __device__ __forceinline__ void pres_issue(const PresArgs<R, SS, SP> &A, unsigne
 }
 
 template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY, bool NL>
-__global__ void __launch_bounds__(BX *BY, 1)
+__global__ void __launch_bounds__(BX *BY, DIM == 3 ? (BY < 8 ? 3 : 2) : 1)
 k_pressure(const PresArgs<R, SS, SP> A)
 {
     using L = PresSmem<R, SS, SP, DIM, NM, BX, BY>;
     constexpr int TW = L::TW, SWX = L::SWX, SHY = L::SHY;
-    static_assert(DIM == 2 || BY >= 7, "the y halo needs 7 thread rows");
     extern __shared__ __align__(128) unsigned char smem[];
 
     const Geo<R> &G = A.g;
@@ -592,6 +621,15 @@ k_pressure(const PresArgs<R, SS, SP> A)
     bool bad = false;
     if (z0 < z1) pres_issue<R, SS, SP, DIM, NM, BX, BY, NL>(A, smem, z0, x0, y, yb, row, hd);
     cp_commit();
+    const bool pml_x = G.wabs > 0 && (x0 < G.wabs || x0 + 3 >= G.nx - G.wabs);
+    const bool pml_y = DIM == 3 && G.wabs > 0 && (y < G.wabs || y >= G.ny - G.wabs);
+    R pdx[4] = {0, 0, 0, 0}, pax[4] = {0, 0, 0, 0}, pdy = 0, pay = 0;
+    if (pml_x && hd)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) { pdx[e] = A.pd[0][x0 + e]; pax[e] = A.pa[0][x0 + e]; }
+    if (pml_y && hd) { pdy = A.pd[1][y]; pay = A.pa[1][y]; }
+    int ccls = -1;
+    R hdr[4], A2[4], B2[4], H2[4];
     for (int k = z0; k < z1; ++k) {
         const long long pk = (long long)k * G.plane;
         const int buf = k & 1;
@@ -601,6 +639,9 @@ k_pressure(const PresArgs<R, SS, SP> A)
         __syncthreads();
         if (k + 1 < z1) pres_issue<R, SS, SP, DIM, NM, BX, BY, NL>(A, smem, k + 1, x0, y, yb, row, hd);
         cp_commit();
+        const bool pml_z = G.wabs > 0 && (k < G.wabs || k >= G.nz - G.wabs);
+        R pdz = 0, paz = 0;
+        if (pml_z) { pdz = A.pd[2][k]; paz = A.pa[2][k]; }
         cp_wait<1>();
         __syncthreads();
         Sm<SS>::ld(reinterpret_cast<const SS *>(st + L::o_qn) + e0, qz[7]);
@@ -641,20 +682,21 @@ k_pressure(const PresArgs<R, SS, SP> A)
             const uint2 cl = *reinterpret_cast<const uint2 *>(reinterpret_cast<const uint16_t *>(st + L::o_cls) + e0);
             const uint16_t cls4[4] = {(uint16_t)(cl.x & 0xffffu), (uint16_t)(cl.x >> 16),
                                       (uint16_t)(cl.y & 0xffffu), (uint16_t)(cl.y >> 16)};
-            R hdr[4], A2[4], B2[4], H2[4];
-            int cprev = -1;
-            const bool pml_x = G.wabs > 0 && (x0 < G.wabs || x0 + 3 >= G.nx - G.wabs);
-            const bool pml_y = DIM == 3 && G.wabs > 0 && (y < G.wabs || y >= G.ny - G.wabs);
-            const bool pml_z = G.wabs > 0 && (k < G.wabs || k >= G.nz - G.wabs);
+            R pp[3][4];
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax) {
+                const bool pml_here = ax == 0 ? pml_x : (ax == 1 ? pml_y : pml_z);
+                if (pml_here) Sm<SS>::ld(reinterpret_cast<const SS *>(st + L::o_pml) + ax * L::TILE + e0, pp[ax]);
+            }
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int c = cls4[e];
-                if (c != cprev) {
+                if (c != ccls) {
                     lut4(A.lut, c, 0, hdr);
                     lut4(A.lut, c, kLutA2, A2);
                     lut4(A.lut, c, kLutB2, B2);
                     lut4(A.lut, c, kLutH2, H2);
-                    cprev = c;
+                    ccls = c;
                 }
                 const bool live = x0 + e < G.nx;
                 R div = qd[0][e] + qd[2][e];
@@ -671,15 +713,13 @@ k_pressure(const PresArgs<R, SS, SP> A)
                     if (DIM == 2 && ax == 1) continue;
                     const bool pml_here = ax == 0 ? pml_x : (ax == 1 ? pml_y : pml_z);
                     if (!pml_here) continue;
-                    const int pos = ax == 0 ? x0 + e : (ax == 1 ? y : k);
-                    const R d = A.pd[ax][pos];
+                    const R d = ax == 0 ? pdx[e] : (ax == 1 ? pdy : pdz);
                     if (d > R(0) && live) {
                         R a, b;
-                        pml_ab(d, A.pa[ax][pos], hdr[1], G.dt, a, b);
-                        SS *pp = A.psip[ax] + pk + row + e;
-                        const R po = Io<SS>::ld1(pp);
+                        pml_ab(d, ax == 0 ? pax[e] : (ax == 1 ? pay : paz), hdr[1], G.dt, a, b);
+                        const R po = pp[ax][e];
                         stp += R(0.5) * (R(1) + b) * po + R(0.5) * a * qd[ax][e];
-                        Io<SS>::st1(pp, SS(b * po + a * qd[ax][e]));
+                        pp[ax][e] = b * po + a * qd[ax][e];
                     }
                 }
                 R fac = kd[e];
@@ -693,6 +733,11 @@ k_pressure(const PresArgs<R, SS, SP> A)
             Io<SS>::st(A.p + pk + row, pv);
 #pragma unroll
             for (int m = 0; m < NM; ++m) Io<SP>::st(A.psi[m] + pk + row, ps[m]);
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax) {
+                const bool pml_here = ax == 0 ? pml_x : (ax == 1 ? pml_y : pml_z);
+                if (pml_here) Io<SS>::st(A.psip[ax] + pk + row, pp[ax]);
+            }
         }
 #pragma unroll
         for (int j = 0; j < 7; ++j)

@@ -7,8 +7,18 @@
 
 namespace fwgb {
 
-template <typename R> struct Tile3 { static constexpr int BX = sizeof(R) == 8 ? 16 : 32, BY = 8; };
-template <typename R> struct Tile2 { static constexpr int BX = 64, BY = 1; };
+// rows of the 3D CTA tiles (tuning knobs, measured best): the velocity sweep
+// runs two 128x4 CTAs per SM, the pressure sweep three 128x4 CTAs per SM
+#ifndef FWGB_VEL3_BY
+#define FWGB_VEL3_BY 4
+#endif
+#ifndef FWGB_PRES3_BY
+#define FWGB_PRES3_BY 4
+#endif
+template <typename R> struct Tile3 {
+    static constexpr int BX = sizeof(R) == 8 ? 16 : 32, BYV = FWGB_VEL3_BY, BYP = FWGB_PRES3_BY;
+};
+template <typename R> struct Tile2 { static constexpr int BX = 64, BYV = 1, BYP = 1; };
 
 template <typename R> Geo<R> make_geo(const fw_medium *m)
 {
@@ -37,23 +47,23 @@ template <typename R, typename SS, typename SP, int DIM, int NM>
 cudaError_t launch_dn(const fw_medium *m, cudaStream_t s, int which)
 {
     constexpr int BX = DIM == 3 ? Tile3<R>::BX : Tile2<R>::BX;
-    constexpr int BY = DIM == 3 ? Tile3<R>::BY : Tile2<R>::BY;
-    using LV = VelSmem<R, SS, SP, DIM, NM, BX, BY>;
-    using LP = PresSmem<R, SS, SP, DIM, NM, BX, BY>;
+    constexpr int BYV = DIM == 3 ? Tile3<R>::BYV : Tile2<R>::BYV;
+    constexpr int BYP = DIM == 3 ? Tile3<R>::BYP : Tile2<R>::BYP;
+    using LV = VelSmem<R, SS, SP, DIM, NM, BX, BYV>;
+    using LP = PresSmem<R, SS, SP, DIM, NM, BX, BYP>;
     if (which & 4) {
-        cudaError_t e = cudaFuncSetAttribute(k_velocity<R, SS, SP, DIM, NM, BX, BY>,
+        cudaError_t e = cudaFuncSetAttribute(k_velocity<R, SS, SP, DIM, NM, BX, BYV>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LV::bytes);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_pressure<R, SS, SP, DIM, NM, BX, BY, true>,
+            e = cudaFuncSetAttribute(k_pressure<R, SS, SP, DIM, NM, BX, BYP, true>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LP::bytes);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_pressure<R, SS, SP, DIM, NM, BX, BY, false>,
+            e = cudaFuncSetAttribute(k_pressure<R, SS, SP, DIM, NM, BX, BYP, false>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LP::bytes);
         return e;
     }
     const Geo<R> g = make_geo<R>(m);
-    dim3 block(BX, BY);
-    dim3 grid((m->NX + 4 * BX - 1) / (4 * BX), (m->NY + BY - 1) / BY, (m->NZ + m->zseg - 1) / m->zseg);
+    const int gx = (m->NX + 4 * BX - 1) / (4 * BX), gz = (m->NZ + m->zseg - 1) / m->zseg;
 
     VelArgs<R, SS, SP> va{};
     va.g = g;
@@ -68,7 +78,8 @@ cudaError_t launch_dn(const fw_medium *m, cudaStream_t s, int which)
     va.rho = static_cast<const SS *>(m->rho);
     va.cls = m->cls;
     va.lut = static_cast<const R *>(m->lut);
-    if (which & 1) k_velocity<R, SS, SP, DIM, NM, BX, BY><<<grid, block, LV::bytes, s>>>(va);
+    if (which & 1)
+        k_velocity<R, SS, SP, DIM, NM, BX, BYV><<<dim3(gx, (m->NY + BYV - 1) / BYV, gz), dim3(BX, BYV), LV::bytes, s>>>(va);
     if (!(which & 2)) return cudaGetLastError();
 
     PresArgs<R, SS, SP> pa{};
@@ -86,10 +97,11 @@ cudaError_t launch_dn(const fw_medium *m, cudaStream_t s, int which)
     pa.cls = m->cls;
     pa.lut = static_cast<const R *>(m->lut);
     pa.mon = m->mon;
+    const dim3 gp(gx, (m->NY + BYP - 1) / BYP, gz), bp(BX, BYP);
     if (m->nonlinear)
-        k_pressure<R, SS, SP, DIM, NM, BX, BY, true><<<grid, block, LP::bytes, s>>>(pa);
+        k_pressure<R, SS, SP, DIM, NM, BX, BYP, true><<<gp, bp, LP::bytes, s>>>(pa);
     else
-        k_pressure<R, SS, SP, DIM, NM, BX, BY, false><<<grid, block, LP::bytes, s>>>(pa);
+        k_pressure<R, SS, SP, DIM, NM, BX, BYP, false><<<gp, bp, LP::bytes, s>>>(pa);
     return cudaGetLastError();
 }
 
