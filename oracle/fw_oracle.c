@@ -211,4 +211,119 @@ int orc_run(const orc_coeffs *g, orc_state *s, int n_steps, int it0,
     return 0;
 }
 
+/* ---------------------------------------------------------------------------
+ * Adjoint (transpose) of one time step, for gradients (linear system: the
+ * nonlinear factor must be off, b2dt == NULL).
+ *
+ * Written as reverse-mode differentiation of velocity_half_step and
+ * pressure_half_step above, statement by statement:
+ *   pressure:  acc = sum_d [ ik2 q_d + sum_nu (old + new)/2 + absorbing ],
+ *              new = b2 old + a2 q_d,  p' = p - kdt acc,  q_d = D-_d v_d;
+ *   velocity:  st = ik1 g + sum_nu (old + new)/2 + absorbing,
+ *              new = b1 old + a1 g,  v' = v - dt_rho st,  g = D+_d p.
+ * The transpose of the staggered derivative with zero values beyond the grid
+ * is minus the other staggered derivative: (D+)^T = -D-, (D-)^T = -D+ (also
+ * for periodic axes).
+ *
+ * f: forward state BEFORE the step; vh: velocity AFTER the step's velocity
+ * half step (the v of the state after the step).  l: adjoint of the state
+ * after the step on entry, of the state before the step on return (receiver
+ * and source terms of the step are applied by the caller first).  dc: the
+ * derivatives of every a, b with respect to the per-voxel factor s on the
+ * d of the tissue mechanisms.  grad_kdt and grad_s accumulate dL/d(K dt) and
+ * dL/ds per voxel.  wq, wg: scratch fields (n points each).  Returns 0, or -1
+ * when the nonlinear factor is on. */
+typedef struct {
+    const double *da1[ORC_MAXMECH][3], *db1[ORC_MAXMECH][3];   /* at v_d points */
+    const double *da2[ORC_MAXMECH][3], *db2[ORC_MAXMECH][3];   /* at p points, per d */
+} orc_dcoeffs;
+
+int orc_adjoint_step(const orc_coeffs *g, const orc_state *f, double *const *vh, orc_state *l,
+                     const orc_dcoeffs *dc, double *grad_kdt, double *grad_s,
+                     double *const *wq, double *const *wg)
+{
+    if (g->b2dt) return -1;
+    /* pressure half step, pointwise: adjoints of acc, psi2, and of q_d into wq */
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int i2 = 0; i2 < g->n[2]; ++i2)
+        for (int i1 = 0; i1 < g->n[1]; ++i1)
+            for (int i0 = 0; i0 < g->n[0]; ++i0) {
+                size_t i = ((size_t)i2 * g->n[1] + i1) * g->n[0] + i0;
+                double lam_acc = -g->kdt[i] * l->p[i];
+                double acc = 0.0, gs = 0.0;
+                for (int d = 0; d < g->ndim; ++d) {
+                    double q = dminus(g, vh[d], i0, i1, i2, d);
+                    double lq = g->ik2[i] * lam_acc;
+                    acc += g->ik2[i] * q;
+                    for (int nu = 0; nu < g->nmech; ++nu) {
+                        double old = f->psi2[nu][d][i];
+                        double nw = g->b2[nu][d][i] * old + g->a2[nu][d][i] * q;
+                        acc += 0.5 * (old + nw);
+                        double lnew = l->psi2[nu][d][i];
+                        lq += g->a2[nu][d][i] * (lnew + 0.5 * lam_acc);
+                        gs += (dc->db2[nu][d][i] * old + dc->da2[nu][d][i] * q) * (lnew + 0.5 * lam_acc);
+                        l->psi2[nu][d][i] = g->b2[nu][d][i] * lnew + 0.5 * (1.0 + g->b2[nu][d][i]) * lam_acc;
+                    }
+                    if (g->a2p[d]) {
+                        double old = f->psi2p[d][i];
+                        double nw = g->b2p[d][i] * old + g->a2p[d][i] * q;
+                        acc += 0.5 * (old + nw);
+                        double lnew = l->psi2p[d][i];
+                        lq += g->a2p[d][i] * (lnew + 0.5 * lam_acc);
+                        l->psi2p[d][i] = g->b2p[d][i] * lnew + 0.5 * (1.0 + g->b2p[d][i]) * lam_acc;
+                    }
+                    wq[d][i] = lq;
+                }
+                grad_kdt[i] += -acc * l->p[i];
+                grad_s[i] += gs;
+            }
+    /* q_d = D-_d v_d: adjoint of v_d gains (D-)^T wq = -D+ wq */
+    for (int d = 0; d < g->ndim; ++d) {
+#pragma omp parallel for collapse(2) schedule(static)
+        for (int i2 = 0; i2 < g->n[2]; ++i2)
+            for (int i1 = 0; i1 < g->n[1]; ++i1)
+                for (int i0 = 0; i0 < g->n[0]; ++i0) {
+                    size_t i = ((size_t)i2 * g->n[1] + i1) * g->n[0] + i0;
+                    l->v[d][i] -= dplus(g, wq[d], i0, i1, i2, d);
+                }
+    }
+    /* velocity half step, pointwise: adjoints of st, psi1, and of g into wg */
+    for (int d = 0; d < g->ndim; ++d) {
+#pragma omp parallel for collapse(2) schedule(static)
+        for (int i2 = 0; i2 < g->n[2]; ++i2)
+            for (int i1 = 0; i1 < g->n[1]; ++i1)
+                for (int i0 = 0; i0 < g->n[0]; ++i0) {
+                    size_t i = ((size_t)i2 * g->n[1] + i1) * g->n[0] + i0;
+                    double lam_st = -g->dt_rho[d][i] * l->v[d][i];
+                    double gd = dplus(g, f->p, i0, i1, i2, d);
+                    double lg = g->ik1[d][i] * lam_st, gs = 0.0;
+                    for (int nu = 0; nu < g->nmech; ++nu) {
+                        double old = f->psi1[nu][d][i];
+                        double lnew = l->psi1[nu][d][i];
+                        lg += g->a1[nu][d][i] * (lnew + 0.5 * lam_st);
+                        gs += (dc->db1[nu][d][i] * old + dc->da1[nu][d][i] * gd) * (lnew + 0.5 * lam_st);
+                        l->psi1[nu][d][i] = g->b1[nu][d][i] * lnew + 0.5 * (1.0 + g->b1[nu][d][i]) * lam_st;
+                    }
+                    if (g->a1p[d]) {
+                        double lnew = l->psi1p[d][i];
+                        lg += g->a1p[d][i] * (lnew + 0.5 * lam_st);
+                        l->psi1p[d][i] = g->b1p[d][i] * lnew + 0.5 * (1.0 + g->b1p[d][i]) * lam_st;
+                    }
+                    wg[d][i] = lg;
+                    grad_s[i] += gs;
+                }
+    }
+    /* g_d = D+_d p: adjoint of p gains (D+)^T wg = -D- wg */
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int i2 = 0; i2 < g->n[2]; ++i2)
+        for (int i1 = 0; i1 < g->n[1]; ++i1)
+            for (int i0 = 0; i0 < g->n[0]; ++i0) {
+                size_t i = ((size_t)i2 * g->n[1] + i1) * g->n[0] + i0;
+                double s = 0.0;
+                for (int d = 0; d < g->ndim; ++d) s += dminus(g, wg[d], i0, i1, i2, d);
+                l->p[i] -= s;
+            }
+    return 0;
+}
+
 int orc_version(void) { return 1; }

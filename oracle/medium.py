@@ -111,7 +111,9 @@ class OracleMedium:
     beta       : nonlinearity map or None
     pml, transition : L_B and L_T in cells (0 = no absorbing layer)
     periodic   : per numpy axis, for the pin tests (no absorbing layer on those axes)
-    dscale     : optional per-voxel factor on every d of the tissue mechanisms
+    dscale     : optional per-voxel factor s on every d of the tissue mechanisms
+                 (d^nu(x) = s(x) d^nu_class), a map like alpha0 and inherited
+                 into the absorbing layer like the other maps
     """
 
     def __init__(self, shape, dx, dt, c, rho, cls, params, beta=None, pml=0, transition=0,
@@ -131,6 +133,7 @@ class OracleMedium:
         cls = inh(cls, np.int64)
         beta = None if beta is None else inh(beta, np.float64)
         self.c, self.rho, self.cls = c, rho, cls
+        self.dscale = None if dscale is None else inh(dscale, np.float64)
         tab = class_table(params)
         self.table = tab
         self.nmech = tab["d1"].shape[1]
@@ -155,7 +158,7 @@ class OracleMedium:
         self.ik2 = 1.0 / k2
         self.a1, self.b1, self.a2, self.b2 = [], [], [], []
         for nu in range(self.nmech):
-            sc = 1.0 if dscale is None else np.asarray(dscale, np.float64)
+            sc = 1.0 if self.dscale is None else self.dscale
             a, b = recursion_ab(tab["d1"][cls, nu] * sc, tab["alpha1"][cls, nu], k1, self.dt)
             self.a1.append(a)
             self.b1.append(b)
