@@ -372,7 +372,7 @@ def run_ours(args):
     t_vel = ms_v.value / K / 1e3
     t_pres = ms_p.value / K / 1e3
     ach = b_vel * vox / t_vel / 1e9
-    traffic = profiled_traffic(vox, "velocity")
+    traffic = profiled_traffic(vox, "velocity" if args.storage == "f32" else "velocity_" + args.storage)
     roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
             "frac": round(ach / peak, 4), "traffic": traffic, "kernel": "k_velocity (velocity sweep)",
             "peak_source": "%s hbm_gbs" % peak_kind}

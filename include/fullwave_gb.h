@@ -55,7 +55,7 @@ extern "C" {
 /* storage of the memory variables psi (fields p, v are FP32 unless F64) */
 #define FW_STORE_F32 0   /* FP32 everything                                   */
 #define FW_STORE_BF16 1  /* psi in bfloat16, FP32 arithmetic                  */
-#define FW_STORE_F16 2   /* psi in binary16 (scaled units), FP32 arithmetic   */
+#define FW_STORE_F16 2   /* psi in binary16, scaled units (see fw_set_sources), FP32 arithmetic */
 #define FW_STORE_F64 3   /* FP64 everything: verification build of the kernels */
 
 /* fields for fw_read_field */
@@ -196,17 +196,18 @@ int fw_create_medium_classes(const fw_grid *g, const float *c, const float *rho,
                              const fw_relax_params *classes, int n_classes, int storage,
                              void *stream, fw_medium **out);
 
-/* Optional per-voxel factor s(x) on every d of the tissue mechanisms
- * (d^nu(x) = s(x) d^nu_class): the map used to take gradients with respect
- * to alpha0(x).  Host or device floats; NULL restores s = 1.  Blocking. */
-int fw_set_dscale(fw_medium *m, const float *s, void *stream);
-
 /* Sources (additive volume sources on p): mask (host, uint8, nx*ny*nz)
  * selects cells in C order; waveforms (host, n_wave x n_steps floats, volume
  * rate [m^D/s]); wave_of_src (host, one int per source in mask order) picks
  * a waveform row, or NULL: one shared row (n_wave = 1) or one row per source
  * (n_wave = n_src).  Time step `it` adds dt*K/dx^D * waveform[it] after the
- * pressure update (nothing once it >= n_steps).  Replaces earlier sources. */
+ * pressure update (nothing once it >= n_steps).  Replaces earlier sources.
+ * FW_STORE_F16 media keep the memory variables in scaled units, psi1 dx /
+ * p_ref and psi2 dx Z / p_ref (Z = 1.54e6 kg/(m^2 s)), so that those of
+ * fields within about 1e-4..1e4 times p_ref stay in the normal range of
+ * binary16; this call sets p_ref to 1/100 of the largest pressure increment
+ * one step of the sources adds (10 Pa before any source) and rescales what
+ * the memory variables already hold. */
 int fw_set_sources(fw_medium *m, const uint8_t *mask, const float *waveforms, int n_wave,
                    int n_steps, const int32_t *wave_of_src);
 

@@ -76,7 +76,6 @@ SIGNATURES = {
                               C.POINTER(_P)]),
     "fw_create_medium_classes": (_I, [C.POINTER(fw_grid), _P, _P, _P, _P, C.POINTER(fw_relax_params), _I, _I,
                                       _P, C.POINTER(_P)]),
-    "fw_set_dscale": (_I, [_P, _P, _P]),
     "fw_set_sources": (_I, [_P, _P, _P, _I, _I, _P]),
     "fw_set_receivers": (_I, [_P, _P, _I, _I]),
     "fw_step": (_I, [_P, _I, _P]),

@@ -168,6 +168,12 @@ __global__ void k_pad(D *dst, const S *src, int nx, int ny, int nz, int px, doub
     }
 }
 
+__global__ void k_scale_half(__half *a, size_t n, float f)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        a[i] = __float2half_rn(__half2float(a[i]) * f);
+}
+
 template <typename T>
 __global__ void k_src_gain(T *gain, const long long *idx, const T *kdt, double inv_dxd, int n)
 {
@@ -278,9 +284,10 @@ int make_dims(const fw_grid *g, int n_mech, int storage, bool nl, Dims *d)
 }
 
 // per-class coefficient table for the run's dt (Eqs. relaxation_a/b), with
-// the midpoint memory-variable update folded in (ceff, hb); psi_scale scales
-// stored memory variables (binary16 storage).
-std::vector<double> build_lut(const std::vector<fw_relax_params> &cl, double dt, double psi_scale)
+// the midpoint memory-variable update folded in (ceff, hb); sc1 and sc2 scale
+// the stored memory variables of the gradient and divergence sides (binary16
+// storage).
+std::vector<double> build_lut(const std::vector<fw_relax_params> &cl, double dt, double sc1, double sc2)
 {
     std::vector<double> t(cl.size() * kLutStride, 0.0);
     for (size_t c = 0; c < cl.size(); ++c) {
@@ -296,12 +303,12 @@ std::vector<double> build_lut(const std::vector<fw_relax_params> &cl, double dt,
             double a2 = p.d2[m] / (p.kappa2 * (p.d2[m] + p.kappa2 * p.alpha2[m])) * (b2 - 1.0);
             ce1 += 0.5 * a1;
             ce2 += 0.5 * a2;
-            e[kLutA1 + m] = a1 * psi_scale;
+            e[kLutA1 + m] = a1 * sc1;
             e[kLutB1 + m] = b1;
-            e[kLutH1 + m] = 0.5 * (1.0 + b1) / psi_scale;
-            e[kLutA2 + m] = a2 * psi_scale;
+            e[kLutH1 + m] = 0.5 * (1.0 + b1) / sc1;
+            e[kLutA2 + m] = a2 * sc2;
             e[kLutB2 + m] = b2;
-            e[kLutH2 + m] = 0.5 * (1.0 + b2) / psi_scale;
+            e[kLutH2 + m] = 0.5 * (1.0 + b2) / sc2;
         }
         e[2] = ce1;
         e[3] = ce2;
@@ -309,11 +316,20 @@ std::vector<double> build_lut(const std::vector<fw_relax_params> &cl, double dt,
     return t;
 }
 
-double psi_scale_of(const fw_medium *m)
+// Stored value of a memory variable = psi * scale.  binary16 storage keeps
+// psi in scaled units so that the memory variables of the expected fields
+// stay in the normal range of the format: the gradient side psi1 (Pa/m) is
+// stored as a pressure difference per cell in units of the reference
+// pressure p_ref (psi1 dx / p_ref), the divergence side psi2 (1/s) as the
+// same with the reference impedance rho c = 1.54e6 kg/(m^2 s)
+// (psi2 dx Z / p_ref).  p_ref follows the sources (fw_set_sources: 1/100 of
+// the largest pressure increment one step of the sources adds, about 1/100
+// of the emitted amplitude; 10 Pa before any source).  Other storages use 1.
+double psi_scale_of(const fw_medium *m, int side)
 {
-    // binary16 memory variables are stored as psi * dx / 1e3 Pa: a per-cell
-    // pressure difference in kPa, which keeps MPa-level fields in range.
-    return m->storage == FW_STORE_F16 ? m->dx / 1e3 : 1.0;
+    if (m->storage != FW_STORE_F16) return 1.0;
+    const double pref = m->psi_pref, zref = 1000.0 * 1540.0;
+    return side == 1 ? m->dx / pref : m->dx * zref / pref;
 }
 
 template <typename T> std::vector<T> cast_vec(const std::vector<double> &v)
@@ -385,7 +401,6 @@ void release(fw_medium *m)
     if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
     dev_free(m->src_buf);
     dev_free(m->rcv_buf);
-    dev_free(m->dscale);
     dev_free(m->slab);
     delete m;
 }
@@ -636,7 +651,7 @@ int create_common(const fw_grid *g, const float *c, const float *rho, const floa
         if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) { release(m); return FW_ERR_CUDA; }
     }
     // class table and absorbing profiles
-    if ((rc = upload_doubles(m, m->lut, build_lut(classes, m->dt, psi_scale_of(m)), s))) { release(m); return rc; }
+    if ((rc = upload_doubles(m, m->lut, build_lut(classes, m->dt, psi_scale_of(m, 1), psi_scale_of(m, 2)), s))) { release(m); return rc; }
     {
         const double r0 = g->pml_r0 > 0 ? g->pml_r0 : 1e-5;
         const double dmax = g->pml > 0 ? -3.0 * m->c_max * std::log(r0) / (2.0 * g->pml * g->dx) : 0.0;
@@ -655,6 +670,34 @@ int create_common(const fw_grid *g, const float *c, const float *rho, const floa
     if (cudaStreamSynchronize(s) != cudaSuccess) { release(m); return FW_ERR_CUDA; }
     m->last_stream = s;
     *out = m;
+    return FW_OK;
+}
+
+// binary16 memory variables: move the pressure reference to 1/100 of the
+// largest per-step source increment max|gain| max|waveform|, rescaling what
+// the memory variables hold and the class table's scaled coefficients.
+int set_psi_reference(fw_medium *m, const float *waveforms, size_t wl)
+{
+    std::vector<float> w(wl), gain(m->n_src);
+    FW_CK(cudaMemcpy(w.data(), waveforms, wl * sizeof(float), cudaMemcpyDefault));
+    FW_CK(cudaMemcpy(gain.data(), m->src_gain, gain.size() * sizeof(float), cudaMemcpyDeviceToHost));
+    double wmax = 0.0, gmax = 0.0;
+    for (float x : w) wmax = std::max(wmax, (double)std::fabs(x));
+    for (float x : gain) gmax = std::max(gmax, (double)std::fabs(x));
+    const double pref = wmax * gmax / 100.0;
+    if (!(pref > 1e-30 && pref < 1e30) || pref == m->psi_pref) return FW_OK;
+    const float f = (float)(m->psi_pref / pref);     // stored ~ 1/p_ref
+    cudaStream_t s = m->last_stream;
+    for (int k = 0; k < m->nmech; ++k) {
+        for (int ax = 0; ax < 3; ++ax)
+            if (m->psi1[k][ax]) k_scale_half<<<grid_blocks(m->vol), 256, 0, s>>>((__half *)m->psi1[k][ax], m->vol, f);
+        k_scale_half<<<grid_blocks(m->vol), 256, 0, s>>>((__half *)m->psi2[k], m->vol, f);
+    }
+    FW_CK(cudaGetLastError());
+    m->psi_pref = pref;
+    int rc = upload_doubles(m, m->lut, build_lut(m->classes, m->dt, psi_scale_of(m, 1), psi_scale_of(m, 2)), s);
+    if (rc) return rc;
+    FW_CK(cudaStreamSynchronize(s));
     return FW_OK;
 }
 
@@ -780,12 +823,6 @@ int fw_create_medium(const fw_grid *g, const float *c, const float *rho, const f
     return create_common(g, c, rho, beta, idx.data(), classes, storage, (cudaStream_t)stream, out);
 }
 
-int fw_set_dscale(fw_medium *m, const float *s, void *stream)
-{
-    (void)m; (void)s; (void)stream;
-    return FW_ERR_UNSUPPORTED;
-}
-
 int fw_set_sources(fw_medium *m, const uint8_t *mask, const float *waveforms, int n_wave, int n_steps,
                    const int32_t *wave_of_src)
 {
@@ -835,6 +872,7 @@ int fw_set_sources(fw_medium *m, const uint8_t *mask, const float *waveforms, in
     m->n_src = ns;
     m->n_wave = n_wave;
     m->wave_len = n_steps;
+    if (m->storage == FW_STORE_F16) return set_psi_reference(m, waveforms, wl);
     return FW_OK;
 }
 
@@ -995,7 +1033,7 @@ int fw_read_field(fw_medium *m, int which, int idx, void *dst, int as_f64, void 
     cudaStream_t s = (cudaStream_t)stream;
     const size_t n = (size_t)m->NX * m->NY * m->NZ;
     const size_t eb = as_f64 ? 8 : 4;
-    const double scale = kind == 1 ? 1.0 / psi_scale_of(m) : 1.0;
+    const double scale = kind == 1 ? 1.0 / psi_scale_of(m, which == FW_FIELD_PSI1 ? 1 : 2) : 1.0;
     DevBuf tmp(n * eb);
     if (!tmp.p) return FW_ERR_NOMEM;
     if (as_f64) FW_CK(unpad_any<double>(m, src, kind, (double *)tmp.p, scale, s));
@@ -1015,7 +1053,7 @@ int fw_write_field(fw_medium *m, int which, int idx, const void *src, int as_f64
     cudaStream_t s = (cudaStream_t)stream;
     const size_t n = (size_t)m->NX * m->NY * m->NZ;
     const size_t eb = as_f64 ? 8 : 4;
-    const double scale = kind == 1 ? psi_scale_of(m) : 1.0;
+    const double scale = kind == 1 ? psi_scale_of(m, which == FW_FIELD_PSI1 ? 1 : 2) : 1.0;
     DevBuf tmp(n * eb);
     if (!tmp.p) return FW_ERR_NOMEM;
     FW_CK(cudaMemcpyAsync(tmp.p, src, n * eb, cudaMemcpyDefault, s));

@@ -49,7 +49,7 @@ struct Graph {
 struct fw_medium {
     fw_grid g{};
     int ndim = 0, nmech = 0, storage = 0;
-    bool nonlinear = false, dscaled = false;
+    bool nonlinear = false;
     int NX = 0, NY = 0, NZ = 0;     // kernel axes: x, y (1 in 2D), depth
     int px = 0;                      // row pitch in elements
     size_t plane = 0, vol = 0;       // elements per plane / per array (padded)
@@ -62,7 +62,7 @@ struct fw_medium {
     size_t slab_bytes = 0;
     void *p = nullptr, *v[3] = {}, *psi1[FW_MAX_MECH][3] = {}, *psi2[FW_MAX_MECH] = {};
     void *psi1p[3] = {}, *psi2p[3] = {};
-    void *kdt = nullptr, *rho = nullptr, *b2dt = nullptr, *lut = nullptr, *dscale = nullptr;
+    void *kdt = nullptr, *rho = nullptr, *b2dt = nullptr, *lut = nullptr;
     void *cdev = nullptr;            // c map (kept for the class coefficient rebuilds)
     uint16_t *cls = nullptr;
     void *prof[3][4] = {};           // per kernel axis: d, alpha at half points; d, alpha at integer points
@@ -83,4 +83,5 @@ struct fw_medium {
     cudaStream_t cap_stream = nullptr;
     std::map<int, fwgb::Graph> graphs;
     int zseg = 32;
+    double psi_pref = 10.0;          // pressure reference [Pa] of binary16 memory variables
 };
