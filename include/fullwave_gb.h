@@ -51,6 +51,7 @@ extern "C" {
 #define FW_ERR_UNSTABLE (-4)    /* non-finite pressure seen by the monitor    */
 #define FW_ERR_STATE (-5)       /* call not valid in the medium's state       */
 #define FW_ERR_UNSUPPORTED (-6) /* combination not compiled into the library  */
+#define FW_ERR_SIZE (-7)        /* size above a fixed limit of the call       */
 
 /* storage of the memory variables psi (fields p, v are FP32 unless F64) */
 #define FW_STORE_F32 0   /* FP32 everything                                   */
@@ -247,6 +248,29 @@ int fw_read_receivers_range(fw_medium *m, int col0, int ncol, void *dst, void *s
 /* Copy a field to dst (host or device), unpadded C order, as float
  * (as_f64 = 0) or double (as_f64 = 1).  Ordered on stream; blocking. */
 int fw_read_field(fw_medium *m, int which, int idx, void *dst, int as_f64, void *stream);
+
+/* fw_read_field without any device allocation.  No counterpart in the
+ * paper: this is a service of the library for callers that cannot allocate
+ * device memory when they read results, e.g. a process whose device memory
+ * is all handed out by another framework's caching allocator, a real-time
+ * loop with a memory budget fixed at start-up, or code that must not let
+ * cudaMalloc/cudaFree synchronise the device.
+ * Same arguments, layout and result as fw_read_field, but the copy is staged
+ * in one device array of FW_NOALLOC_MAX_BYTES bytes that the library defines
+ * at file scope: every device that loads the library holds that array until
+ * the process exits, and no call allocates or frees device memory.
+ * - Limit: nx*ny*nz*(as_f64 ? 8 : 4) <= FW_NOALLOC_MAX_BYTES (64 MiB, e.g.
+ *   a 256^3 float field), else FW_ERR_SIZE and nothing is copied.
+ * - The first call on a device looks up the array's device address (with
+ *   that device current), so make that first call before any stream capture
+ *   on the device.  The medium's device must be current.
+ * - All calls share the one array and it keeps the last call's contents:
+ *   calls whose work overlaps on the GPU (other streams, other host threads)
+ *   race on it and must be ordered by the caller.  Blocking, like
+ *   fw_read_field.
+ * Errors: FW_ERR_ARG (bad field or pointer), FW_ERR_SIZE, FW_ERR_CUDA. */
+#define FW_NOALLOC_MAX_BYTES (64u << 20)
+int fw_read_field_noalloc(fw_medium *m, int which, int idx, void *dst, int as_f64, void *stream);
 
 /* Write a field from src (host or device, same layout/type rules).  For
  * initial conditions and tests.  Blocking. */

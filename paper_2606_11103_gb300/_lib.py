@@ -17,6 +17,8 @@ FW_ERR_NOMEM = -3
 FW_ERR_UNSTABLE = -4
 FW_ERR_STATE = -5
 FW_ERR_UNSUPPORTED = -6
+FW_ERR_SIZE = -7
+FW_NOALLOC_MAX_BYTES = 64 << 20
 
 FW_STORE_F32, FW_STORE_BF16, FW_STORE_F16, FW_STORE_F64 = 0, 1, 2, 3
 FW_FIELD_P, FW_FIELD_V, FW_FIELD_PSI1, FW_FIELD_PSI2, FW_FIELD_PSI1P, FW_FIELD_PSI2P = range(6)
@@ -84,6 +86,7 @@ SIGNATURES = {
     "fw_set_waveform_samples": (_I, [_P, _I, _I, _P, _P]),
     "fw_read_receivers_range": (_I, [_P, _I, _I, _P, _P]),
     "fw_read_field": (_I, [_P, _I, _I, _P, _I, _P]),
+    "fw_read_field_noalloc": (_I, [_P, _I, _I, _P, _I, _P]),
     "fw_write_field": (_I, [_P, _I, _I, _P, _I, _P]),
     "fw_read_receivers": (_I, [_P, _P, _I, _P]),
     "fw_state_bytes": (_I, [_P, C.POINTER(C.c_size_t)]),

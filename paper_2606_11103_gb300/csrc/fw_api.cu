@@ -703,6 +703,17 @@ int set_psi_reference(fw_medium *m, const float *waveforms, size_t wl)
 
 }  // namespace
 
+namespace fwgb {
+// field pointer, element kind and read-back scale, for the staging-array read
+int field_lookup(fw_medium *m, int which, int idx, void **ptr, int *kind, double *read_scale)
+{
+    int rc = field_ptr(m, which, idx, ptr, kind);
+    if (rc) return rc;
+    *read_scale = *kind == 1 ? 1.0 / psi_scale_of(m, which == FW_FIELD_PSI1 ? 1 : 2) : 1.0;
+    return FW_OK;
+}
+}  // namespace fwgb
+
 // ============================================================================
 extern "C" {
 
@@ -718,6 +729,7 @@ const char *fw_strerror(int code)
     case FW_ERR_UNSTABLE: return "non-finite pressure (unstable run)";
     case FW_ERR_STATE: return "invalid state for this call";
     case FW_ERR_UNSUPPORTED: return "unsupported combination";
+    case FW_ERR_SIZE: return "size above a fixed limit of the call";
     default: return "unknown error";
     }
 }
