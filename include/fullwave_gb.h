@@ -288,6 +288,36 @@ int fw_state_bytes(fw_medium *m, size_t *bytes);
 int fw_save_state(fw_medium *m, void *dst, void *stream);
 int fw_load_state(fw_medium *m, const void *src, void *stream);
 
+/* Gradient of a receiver functional with respect to the sound-speed map
+ * c(x) and the attenuation map alpha0(x), by the discrete adjoint of the
+ * time step (the transpose of the velocity and pressure sweeps of Sec. 2.1
+ * with the discretisation of Sec. 3.3); the paper names inverse problems as
+ * the use of the forward model but prints no gradient method.
+ * Runs n_steps forward from the medium's current state exactly as fw_run
+ * (traces recorded, the medium ends n_steps later), keeping a state image
+ * every checkpoint_every steps (<= 0: sqrt(n_steps)), then runs the adjoint
+ * backwards, recomputing each segment's states from its checkpoint, and
+ * returns dL/dc and dL/dalpha0 for
+ *     L = sum_{r, col} G[r][col] * trace[r][col],
+ * G = dL/dtraces, [n_rcv][n_rec] (e.g. trace - d_obs for the misfit
+ * 1/2 |trace - d_obs|^2); columns not recorded in this window do not count.
+ * Readings: c enters through K dt = rho c^2 dt (update and source gain);
+ * dt, the absorbing profile and the class relaxation sets stay fixed;
+ * alpha0 scales the d of the voxel's class, d^nu(x) = d^nu_class alpha0(x) /
+ * alpha0_class, kappa and alpha^nu fixed, so dL/dalpha0 = dL/ds / alpha0
+ * with s that factor; the absorbing layer's inherited maps fold back onto
+ * the cells they copy.  The state at the start of the window is held fixed.
+ * alpha0: the medium's alpha0 map [nx*ny*nz] (host or device), or NULL: then
+ * grad_alpha0 receives dL/ds.  G, alpha0, grad_c, grad_alpha0 are float
+ * (as_f64 = 0) or double (as_f64 = 1), C order, host or device; grad_c or
+ * grad_alpha0 may be NULL.  Device memory: (ceil(n_steps/K) + K + 3) state
+ * images (fw_state_bytes) plus 6 fields and 4 FP64 maps, from the installed
+ * allocator, released before return.  Blocking.
+ * Errors: FW_ERR_ARG, FW_ERR_UNSUPPORTED (nonlinear media, 16-bit storage),
+ * FW_ERR_NOMEM, FW_ERR_CUDA, or the medium's sticky error. */
+int fw_gradient(fw_medium *m, int n_steps, int checkpoint_every, const void *G, const void *alpha0,
+                void *grad_c, void *grad_alpha0, int as_f64, void *stream);
+
 /* Stability monitor (non-finite pressure, Sec. 4.6): synchronises the
  * medium's last stream and returns FW_OK or FW_ERR_UNSTABLE (sticky);
  * max_abs_p (may be NULL) receives max |p| seen since creation. */

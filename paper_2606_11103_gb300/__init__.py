@@ -244,6 +244,21 @@ class Medium:
         check(lib().fw_read_receivers(self.h, ptr, int(bool(f64)), _stream(stream)), "fw_read_receivers")
         return out
 
+    def gradient(self, n_steps, G, alpha0=None, checkpoint=0, f64=False, out=None, stream=None):
+        """fw_gradient: run n_steps forward (as run()) and return (dL/dc,
+        dL/dalpha0) of L = sum G * traces on the user grid.  G [n_rcv, n_rec];
+        alpha0 the medium's alpha0 map, or None for dL/ds.  Host (numpy) or
+        device (torch) buffers; ``out`` = (grad_c, grad_alpha0) to fill."""
+        dt = np.float64 if f64 else np.float32
+        bG = _Buf(G, dt)
+        ba = _Buf(alpha0, dt) if alpha0 is not None else None
+        if out is None:
+            out = (np.empty(self.shape, dt), np.empty(self.shape, dt))
+        ptrs = [C.c_void_p(o.data_ptr()) if hasattr(o, "data_ptr") else C.c_void_p(o.ctypes.data) for o in out]
+        check(lib().fw_gradient(self.h, int(n_steps), int(checkpoint), bG.ptr, ba.ptr if ba else None,
+                                ptrs[0], ptrs[1], int(bool(f64)), _stream(stream)), "fw_gradient")
+        return out
+
     def state_bytes(self):
         n = C.c_size_t()
         check(lib().fw_state_bytes(self.h, C.byref(n)), "fw_state_bytes")

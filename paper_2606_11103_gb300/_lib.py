@@ -92,6 +92,7 @@ SIGNATURES = {
     "fw_state_bytes": (_I, [_P, C.POINTER(C.c_size_t)]),
     "fw_save_state": (_I, [_P, _P, _P]),
     "fw_load_state": (_I, [_P, _P, _P]),
+    "fw_gradient": (_I, [_P, _I, _I, _P, _P, _P, _P, _I, _P]),
     "fw_status": (_I, [_P, C.POINTER(C.c_float)]),
     "fw_medium_get_info": (_I, [_P, C.POINTER(fw_medium_info)]),
     "fw_destroy_medium": (None, [_P]),

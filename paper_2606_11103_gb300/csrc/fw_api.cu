@@ -704,6 +704,18 @@ int set_psi_reference(fw_medium *m, const float *waveforms, size_t wl)
 }  // namespace
 
 namespace fwgb {
+// device memory through the installed allocator, and the size of the state
+// image (the checkpoint image without the step counter), for the adjoint
+void *device_alloc(size_t bytes) { return dev_alloc(bytes); }
+void device_free(void *p) { dev_free(p); }
+size_t state_image_bytes(const fw_medium *m)
+{
+    Dims d{m->ndim, m->NX, m->NY, m->NZ, m->px, m->es, m->eps, m->wabs, m->nmech, m->plane, m->vol, m->nonlinear};
+    return make_layout(d, m->n_classes).off_state_end;
+}
+}  // namespace fwgb
+
+namespace fwgb {
 // field pointer, element kind and read-back scale, for the staging-array read
 int field_lookup(fw_medium *m, int which, int idx, void **ptr, int *kind, double *read_scale)
 {
