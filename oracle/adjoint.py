@@ -130,13 +130,14 @@ class Adjoint:
         self.med = med
         tab, cls, dt = med.table, med.cls, med.dt
         s = 1.0 if med.dscale is None else med.dscale
+        ramp = med.ramp
         k1 = tab["kappa1"][cls]
         k2 = tab["kappa2"][cls]
         self._keep = []
         dc = _DCoeffs()
         for nu in range(med.nmech):
-            da1, db1 = recursion_ab_dscale(tab["d1"][cls, nu], tab["alpha1"][cls, nu], k1, dt, s)
-            da2, db2 = recursion_ab_dscale(tab["d2"][cls, nu], tab["alpha2"][cls, nu], k2, dt, s)
+            da1, db1 = recursion_ab_dscale(tab["d1"][cls, nu] * ramp, tab["alpha1"][cls, nu], k1, dt, s)
+            da2, db2 = recursion_ab_dscale(tab["d2"][cls, nu] * ramp, tab["alpha2"][cls, nu], k2, dt, s)
             arrs = [np.ascontiguousarray(np.broadcast_to(a, med.shape), np.float64) for a in (da1, db1, da2, db2)]
             self._keep += arrs
             for d in range(med.ndim):

@@ -19,6 +19,17 @@
       d_max = -3 c_max ln(R0) / (2 L_B dx),  R0 = 1e-5,
       alpha(s) = pi f0 (1 - s/(L_T+L_B)),
   and kappa of the mechanism = the tissue kappa of the point's stretch.
+* two-stage layer (Sec. 4.4 methods, Sec. 5.4): the tissue ("higher-order")
+  relaxation mechanisms are ramped across the transition region, and within
+  the absorbing region when there is no transition layer, so that the
+  absorbing mechanism alone acts at the outer edge.  Reading of the ramp:
+  every tissue d^nu of a cell is multiplied by
+      r(s) = 1 - (s / L_r)^2  for s < L_r,   0 beyond,
+  with s the cell's depth into the layer (the largest over the axes, at the
+  cell centre) and L_r = L_T, or L_B when L_T = 0.  Without it, tissue
+  mechanisms added to a strong absorbing mechanism whose alpha vanishes at
+  the outer edge make the low-frequency stretch negative there, and long
+  runs diverge (the paper's no-transition variant diverged in 29 cells).
 * time step from a CFL number: dt = CFL dx / max(c / sqrt(kappa_1 kappa_2)).
 """
 from __future__ import annotations
@@ -88,6 +99,19 @@ def absorbing_depth(n, width, staggered):
     return np.maximum(0.0, np.maximum(left, right))
 
 
+def tissue_ramp(shape, width, l_t, l_b, axes):
+    """Factor r(s) on the tissue d^nu of every cell (1 in the interior)."""
+    s = np.zeros(shape)
+    if width <= 0:
+        return np.ones(shape)
+    for ax in axes:
+        bshape = [1] * len(shape)
+        bshape[ax] = shape[ax]
+        s = np.maximum(s, absorbing_depth(shape[ax], width, False).reshape(bshape))
+    lr = l_t if l_t > 0 else 0.5 * l_b
+    return np.where(s < lr, 1.0 - (s / lr) ** 2, 0.0)
+
+
 def absorbing_profile(s, l_t, l_b, d_max, f0):
     s = np.asarray(s, dtype=np.float64)
     if l_t > 0:
@@ -111,13 +135,15 @@ class OracleMedium:
     beta       : nonlinearity map or None
     pml, transition : L_B and L_T in cells (0 = no absorbing layer)
     periodic   : per numpy axis, for the pin tests (no absorbing layer on those axes)
+    tissue_ramp_on : ramp the tissue mechanisms across the layer (the method);
+                 False only to show what happens without it
     dscale     : optional per-voxel factor s on every d of the tissue mechanisms
                  (d^nu(x) = s(x) d^nu_class), a map like alpha0 and inherited
                  into the absorbing layer like the other maps
     """
 
     def __init__(self, shape, dx, dt, c, rho, cls, params, beta=None, pml=0, transition=0,
-                 f0=3e6, R0=1e-5, periodic=None, dscale=None):
+                 f0=3e6, R0=1e-5, periodic=None, dscale=None, tissue_ramp_on=True):
         self.shape = tuple(shape)
         self.ndim = len(shape)
         self.dx, self.dt = float(dx), float(dt)
@@ -157,8 +183,10 @@ class OracleMedium:
         self.ik1 = 1.0 / k1
         self.ik2 = 1.0 / k2
         self.a1, self.b1, self.a2, self.b2 = [], [], [], []
+        self.ramp = tissue_ramp(self.shape, width, transition, pml, self.abs_axes) if tissue_ramp_on \
+            else np.ones(self.shape)
         for nu in range(self.nmech):
-            sc = 1.0 if self.dscale is None else self.dscale
+            sc = self.ramp if self.dscale is None else self.dscale * self.ramp
             a, b = recursion_ab(tab["d1"][cls, nu] * sc, tab["alpha1"][cls, nu], k1, self.dt)
             self.a1.append(a)
             self.b1.append(b)

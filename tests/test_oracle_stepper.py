@@ -423,3 +423,32 @@ def test_fubini_second_harmonic(oracle_lib):
     assert 0.1 < s2 < 0.5
     assert 0.5 * p0 < p_meas < 1.5 * p0
     assert abs(got / want - 1) < 0.05, (got, want)
+
+
+def test_tissue_ramp_keeps_the_absorbing_layer_stable(oracle_lib):
+    """Long-time stability of the absorbing layer (Sec. 5.4: the transition
+    layer removes the divergent cells).  A point source in a strongly lossy
+    medium (alpha0 1.0, y 2.0, N = 4) with a 20-cell layer and no transition:
+    with the tissue mechanisms ramped out across the layer the field decays
+    after the pulse has left; with them kept at full strength up to the
+    outer edge, where the absorbing mechanism's alpha vanishes, the
+    low-frequency stretch turns negative there and the run diverges."""
+    prm, _ = fit.fit_relaxation(1.0, 2.0, 4, maxiter=3000, w_list=(0.1, 0.5, 0.9))
+    f0 = 3e6
+    dx = 1540.0 / (f0 * 12)
+    dt = 0.4 * dx / 1700.0
+    shape = (96, 96)
+    out = {}
+    for ramp in (True, False):
+        med = OracleMedium(shape, dx, dt, np.full(shape, 1540.0), np.full(shape, 1000.0), np.zeros(shape, np.int64),
+                           [prm], pml=20, f0=f0, tissue_ramp_on=ramp)
+        sim = OracleSim(med)
+        src = np.zeros(shape, np.uint8)
+        src[48, 48] = 1
+        sim.set_sources(src, gaussian_pulse(f0, dt, 1200, 1e-6)[None])
+        sim.run(100)
+        peak = np.abs(sim.p).max()
+        sim.run(1100)
+        out[ramp] = np.abs(sim.p).max() / peak
+    assert out[True] < 1e-4, out
+    assert out[False] > 1e3, out
