@@ -136,8 +136,10 @@ class Adjoint:
         self._keep = []
         dc = _DCoeffs()
         for nu in range(med.nmech):
-            da1, db1 = recursion_ab_dscale(tab["d1"][cls, nu] * ramp, tab["alpha1"][cls, nu], k1, dt, s)
-            da2, db2 = recursion_ab_dscale(tab["d2"][cls, nu] * ramp, tab["alpha2"][cls, nu], k2, dt, s)
+            # the layer ramp scales a (not b): a = r a_class(d s), so da/ds = r da_class/ds
+            da1, db1 = recursion_ab_dscale(tab["d1"][cls, nu], tab["alpha1"][cls, nu], k1, dt, s)
+            da2, db2 = recursion_ab_dscale(tab["d2"][cls, nu], tab["alpha2"][cls, nu], k2, dt, s)
+            da1, da2 = da1 * ramp, da2 * ramp
             arrs = [np.ascontiguousarray(np.broadcast_to(a, med.shape), np.float64) for a in (da1, db1, da2, db2)]
             self._keep += arrs
             for d in range(med.ndim):

@@ -23,13 +23,16 @@
   relaxation mechanisms are ramped across the transition region, and within
   the absorbing region when there is no transition layer, so that the
   absorbing mechanism alone acts at the outer edge.  Reading of the ramp:
-  every tissue d^nu of a cell is multiplied by
+  the strength of every tissue mechanism of a cell is multiplied by
       r(s) = 1 - (s / L_r)^2  for s < L_r,   0 beyond,
-  with s the cell's depth into the layer (the largest over the axes, at the
-  cell centre) and L_r = L_T, or L_B when L_T = 0.  Without it, tissue
-  mechanisms added to a strong absorbing mechanism whose alpha vanishes at
-  the outer edge make the low-frequency stretch negative there, and long
-  runs diverge (the paper's no-transition variant diverged in 29 cells).
+  with its relaxation rate d/kappa + alpha held fixed, i.e. d -> r d and
+  alpha -> alpha + (1 - r) d / kappa, which gives a -> r a with b unchanged
+  in Eqs. relaxation_a/b; s is the cell's depth into the layer (the largest
+  over the axes, at the cell centre), L_r = L_T, or L_B / 2 when L_T = 0.
+  Without it, tissue mechanisms added to a strong absorbing mechanism whose
+  alpha vanishes at the outer edge make the low-frequency stretch negative
+  there, and long runs diverge (the paper's no-transition variant diverged
+  in 29 cells).
 * time step from a CFL number: dt = CFL dx / max(c / sqrt(kappa_1 kappa_2)).
 """
 from __future__ import annotations
@@ -100,7 +103,8 @@ def absorbing_depth(n, width, staggered):
 
 
 def tissue_ramp(shape, width, l_t, l_b, axes):
-    """Factor r(s) on the tissue d^nu of every cell (1 in the interior)."""
+    """Factor r(s) on the strength of the tissue mechanisms of every cell
+    (1 in the interior)."""
     s = np.zeros(shape)
     if width <= 0:
         return np.ones(shape)
@@ -186,12 +190,13 @@ class OracleMedium:
         self.ramp = tissue_ramp(self.shape, width, transition, pml, self.abs_axes) if tissue_ramp_on \
             else np.ones(self.shape)
         for nu in range(self.nmech):
-            sc = self.ramp if self.dscale is None else self.dscale * self.ramp
+            sc = 1.0 if self.dscale is None else self.dscale
+            # ramp: d -> r d at a fixed relaxation rate, i.e. a -> r a, b unchanged
             a, b = recursion_ab(tab["d1"][cls, nu] * sc, tab["alpha1"][cls, nu], k1, self.dt)
-            self.a1.append(a)
+            self.a1.append(a * self.ramp)
             self.b1.append(b)
             a, b = recursion_ab(tab["d2"][cls, nu] * sc, tab["alpha2"][cls, nu], k2, self.dt)
-            self.a2.append(a)
+            self.a2.append(a * self.ramp)
             self.b2.append(b)
         # absorbing mechanism per direction
         self.a1p = [None] * self.ndim
