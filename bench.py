@@ -68,12 +68,19 @@ def barrier(ws):
         dist.barrier()
 
 
+def replica_value(units_per_rank, seconds_per_rank, ws):
+    """Whole-job throughput of N independent replicas: the units all ranks
+    processed divided by the slowest rank's time (weak scaling)."""
+    return ws * units_per_rank / allmax(seconds_per_rank, ws)
+
+
 def allmax(x, ws):
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -343,7 +350,7 @@ def run_ours(args):
     rc, pmax = m.status()
     if rc != 0:
         raise RuntimeError("unstable run: %s" % fw.FwError(rc))
-    value = ws * vox * K / (ms / 1e3) / 1e9
+    value = replica_value(vox * K, ms_tot.value / 1e3, ws) / 1e9
 
     # ---- end to end through the C ABI: per step, the step's waveform samples
     # go host->device from pinned memory and the step's receiver samples come
