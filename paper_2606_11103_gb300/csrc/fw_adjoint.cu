@@ -20,6 +20,8 @@
 //             p' = p - K dt stp,  div = sum_d D-_d v_d;
 //   velocity: st = ceff1 g + sum hb1 psi1 + absorbing, psi1' = b1 psi1 + a1 g,
 //             v' = v - dtr st,  g = D+_d p;
+// (in the absorbing layer a -> r a and ceff -> 1/kappa + r (ceff - 1/kappa),
+// r the tissue ramp of the cell);
 // with (D+)^T = -D- and (D-)^T = -D+ for zero values beyond the grid.
 // One reverse step is five launches: receiver injection, source-gain
 // gradient, pressure adjoint (pointwise, writes the adjoint of q_d), velocity
@@ -50,6 +52,8 @@ template <typename R> struct AdjArgs {
     long long plane, vol;
     bool ax_on[3];
     R c1, c2, c3, c4, dt;
+    int wabs;          // absorbing width (0: none) and 1 / length of the tissue ramp
+    R inv_lr;
     // adjoint state
     R *lp, *lv[3], *lpsi1[kMaxMech][3], *lpsi2[kMaxMech], *lpsi1p[3], *lpsi2p[3];
     // forward state before the step (f) and velocity after it (fv1)
@@ -103,6 +107,16 @@ __device__ __forceinline__ R dminus(const AdjArgs<R> &A, const R *f, long long i
            A.c4 * (at(c + 3) - at(c - 4));
 }
 
+// tissue-mechanism strength of the cell (the forward sweeps' ramp, same arithmetic)
+template <typename R>
+__device__ __forceinline__ R cell_ramp(const AdjArgs<R> &A, const Pt<R> &P)
+{
+    if (A.wabs <= 0) return R(1);
+    const R s = fmax(fmax(layer_depth<R>(P.c[0], A.nx, A.wabs), layer_depth<R>(P.c[1], A.ny, A.wabs)),
+                     layer_depth<R>(P.c[2], A.nz, A.wabs));
+    return ramp_of(s, A.inv_lr);
+}
+
 template <typename R>
 __global__ void k_adj_pres(const AdjArgs<R> A)
 {
@@ -120,15 +134,19 @@ __global__ void k_adj_pres(const AdjArgs<R> A)
             }
         const R lp = A.lp[i];
         const R lst = -A.kdt[i] * lp;
-        R stp = div * t[3];
-        R ldiv = t[3] * lst;
+        // tissue ramp of the absorbing layer: a -> r a (the forward sweep's ce, r div)
+        const R r = cell_ramp(A, P);
+        const R ik2 = fw_rcp(t[1]);
+        const R ce = r == R(1) ? t[3] : ik2 + r * (t[3] - ik2);
+        R stp = div * ce;
+        R ldiv = ce * lst;
         double gs = 0.0;
         for (int m = 0; m < A.nmech; ++m) {
             const R old = A.fpsi2[m][i];
             stp += t[kLutH2 + m] * old;
             const R ln = A.lpsi2[m][i];
-            ldiv += t[kLutA2 + m] * ln;
-            gs += double(dtb[12 + m] * old + dtb[8 + m] * div) * double(ln + R(0.5) * lst);
+            ldiv += r * t[kLutA2 + m] * ln;
+            gs += double(dtb[12 + m] * old + r * dtb[8 + m] * div) * double(ln + R(0.5) * lst);
             A.lpsi2[m][i] = t[kLutB2 + m] * ln + t[kLutH2 + m] * lst;
         }
         for (int ax = 0; ax < 3; ++ax) {
@@ -163,6 +181,9 @@ __global__ void k_adj_vel(const AdjArgs<R> A)
         const R *t = A.lut + (size_t)A.cls[i] * kLutStride;
         const R *dtb = A.dlut + (size_t)A.cls[i] * kDStride;
         const R own = A.rho[i];
+        const R r = cell_ramp(A, P);
+        const R ik1 = fw_rcp(t[0]);
+        const R ce = r == R(1) ? t[2] : ik1 + r * (t[2] - ik1);
         double gs = 0.0;
         for (int ax = 0; ax < 3; ++ax) {
             if (!A.ax_on[ax]) continue;
@@ -173,12 +194,12 @@ __global__ void k_adj_vel(const AdjArgs<R> A)
             const R dtr = R(2) * A.dt * fw_rcp(own + nxt);
             const R lst = -dtr * lv;
             const R g = dplus(A, A.fp, i, c, n, st);
-            R lg = t[2] * lst;
+            R lg = ce * lst;
             for (int m = 0; m < A.nmech; ++m) {
                 const R old = A.fpsi1[m][ax][i];
                 const R ln = A.lpsi1[m][ax][i];
-                lg += t[kLutA1 + m] * ln;
-                gs += double(dtb[4 + m] * old + dtb[m] * g) * double(ln + R(0.5) * lst);
+                lg += r * t[kLutA1 + m] * ln;
+                gs += double(dtb[4 + m] * old + r * dtb[m] * g) * double(ln + R(0.5) * lst);
                 A.lpsi1[m][ax][i] = t[kLutB1 + m] * ln + t[kLutH1 + m] * lst;
             }
             if (A.pdh[ax]) {
@@ -378,6 +399,8 @@ int gradient_impl(fw_medium *m, int n_steps, int K, const void *G, const void *a
     const double cm[4] = {1225.0 / 1024.0, -245.0 / 3072.0, 49.0 / 5120.0, -5.0 / 7168.0};
     A.c1 = R(cm[0] / m->dx); A.c2 = R(cm[1] / m->dx); A.c3 = R(cm[2] / m->dx); A.c4 = R(cm[3] / m->dx);
     A.dt = R(m->dt);
+    A.wabs = m->wabs;
+    A.inv_lr = m->wabs > 0 ? R(1) / R(m->g.transition > 0 ? m->g.transition : 0.5 * m->g.pml) : R(0);
     char *L = static_cast<char *>(lam.p);
     A.lp = reinterpret_cast<R *>(L + off(m->p));
     for (int ax = 0; ax < 3; ++ax) {

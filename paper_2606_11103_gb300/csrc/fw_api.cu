@@ -613,8 +613,10 @@ int create_common(const fw_grid *g, const float *c, const float *rho, const floa
         for (size_t i = 0; i < classes.size(); ++i) sc[i] = 1.0 / std::sqrt(classes[i].kappa1 * classes[i].kappa2);
         DevBuf dsc(sc.size() * sizeof(double)), dmx(2 * sizeof(unsigned int));
         if (!dsc.p || !dmx.p) { release(m); return FW_ERR_NOMEM; }
-        if (cudaMemcpy(dsc.p, sc.data(), sc.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemset(dmx.p, 0, 8) != cudaSuccess) { release(m); return FW_ERR_CUDA; }
+        // stream-ordered uploads: the kernel below runs on s, which need not
+        // wait for the legacy stream
+        if (cudaMemcpyAsync(dsc.p, sc.data(), sc.size() * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemsetAsync(dmx.p, 0, 8, s) != cudaSuccess) { release(m); return FW_ERR_CUDA; }
         if (d.es == 8) k_cmax<double><<<grid_blocks(d.vol), 256, 0, s>>>((const double *)m->cdev, m->cls, (const double *)dsc.p, d.vol, (unsigned *)dmx.p);
         else k_cmax<float><<<grid_blocks(d.vol), 256, 0, s>>>((const float *)m->cdev, m->cls, (const double *)dsc.p, d.vol, (unsigned *)dmx.p);
         unsigned hm[2];
@@ -880,19 +882,23 @@ int fw_set_sources(fw_medium *m, const uint8_t *mask, const float *waveforms, in
     m->src_gain = b + o_gain;
     m->wave_of = reinterpret_cast<int *>(b + o_wof);
     m->waves = b + o_wave;
-    FW_CK(cudaMemcpy(m->src_idx, idx.data(), ns * 8, cudaMemcpyHostToDevice));
-    FW_CK(cudaMemcpy(m->wave_of, wof.data(), ns * 4, cudaMemcpyHostToDevice));
+    // every upload is ordered on the medium's stream and complete before
+    // return: later work on any other (non-blocking) stream reads these
+    // arrays without waiting for the legacy stream
+    std::vector<double> w64;
+    FW_CK(cudaMemcpyAsync(m->src_idx, idx.data(), ns * 8, cudaMemcpyHostToDevice, s));
+    FW_CK(cudaMemcpyAsync(m->wave_of, wof.data(), ns * 4, cudaMemcpyHostToDevice, s));
     if (m->es == 8) {
-        std::vector<double> w(waveforms, waveforms + wl);
-        FW_CK(cudaMemcpy(m->waves, w.data(), wl * 8, cudaMemcpyHostToDevice));
+        w64.assign(waveforms, waveforms + wl);
+        FW_CK(cudaMemcpyAsync(m->waves, w64.data(), wl * 8, cudaMemcpyHostToDevice, s));
     } else {
-        FW_CK(cudaMemcpy(m->waves, waveforms, wl * 4, cudaMemcpyDefault));
+        FW_CK(cudaMemcpyAsync(m->waves, waveforms, wl * 4, cudaMemcpyDefault, s));
     }
     const double inv = 1.0 / std::pow(m->dx, m->ndim);
-    if (m->es == 8) k_src_gain<double><<<(ns + 255) / 256, 256>>>((double *)m->src_gain, m->src_idx, (const double *)m->kdt, inv, ns);
-    else k_src_gain<float><<<(ns + 255) / 256, 256>>>((float *)m->src_gain, m->src_idx, (const float *)m->kdt, inv, ns);
+    if (m->es == 8) k_src_gain<double><<<(ns + 255) / 256, 256, 0, s>>>((double *)m->src_gain, m->src_idx, (const double *)m->kdt, inv, ns);
+    else k_src_gain<float><<<(ns + 255) / 256, 256, 0, s>>>((float *)m->src_gain, m->src_idx, (const float *)m->kdt, inv, ns);
     FW_CK(cudaGetLastError());
-    FW_CK(cudaDeviceSynchronize());
+    FW_CK(cudaStreamSynchronize(s));
     m->n_src = ns;
     m->n_wave = n_wave;
     m->wave_len = n_steps;
@@ -920,8 +926,10 @@ int fw_set_receivers(fw_medium *m, const uint8_t *mask, int decim, int n_steps)
     char *b = static_cast<char *>(m->rcv_buf);
     m->rcv_idx = reinterpret_cast<long long *>(b);
     m->traces = b + o_tr;
-    FW_CK(cudaMemcpy(m->rcv_idx, idx.data(), nr * 8, cudaMemcpyHostToDevice));
-    FW_CK(cudaMemset(m->traces, 0, (size_t)nr * std::max(nrec, 1) * m->es));
+    // ordered on the medium's stream and complete before return (see fw_set_sources)
+    FW_CK(cudaMemcpyAsync(m->rcv_idx, idx.data(), nr * 8, cudaMemcpyHostToDevice, s));
+    FW_CK(cudaMemsetAsync(m->traces, 0, (size_t)nr * std::max(nrec, 1) * m->es, s));
+    FW_CK(cudaStreamSynchronize(s));
     m->n_rcv = nr;
     m->n_rec = nrec;
     m->decim = decim;
@@ -1154,6 +1162,7 @@ int fw_status(fw_medium *m, float *max_abs_p)
     FW_CK(cudaMemcpy(&h, m->mon, sizeof(Monitor), cudaMemcpyDeviceToHost));
     if (max_abs_p) std::memcpy(max_abs_p, &h.max_bits, 4);
     if (h.nonfinite) m->sticky = FW_ERR_UNSTABLE;
+    if (h.bad_index) m->sticky = FW_ERR_STATE;
     return m->sticky;
 }
 

@@ -37,6 +37,7 @@ constexpr int kLutA1 = 4, kLutB1 = 8, kLutH1 = 12, kLutA2 = 16, kLutB2 = 20, kLu
 struct Monitor {
     unsigned int max_bits;   // bits of max |p| (non-negative float)
     int nonfinite;
+    int bad_index;           // a source/receiver index or step counter out of range (skipped)
 };
 
 struct Graph {

@@ -224,7 +224,28 @@ template <typename R> struct Geo {
     int wabs;            // absorbing width in cells (0: none)
     R c1, c2, c3, c4;    // stencil weights / dx
     R dt;
+    R lr;                // length [cells] of the tissue-mechanism ramp in the layer
 };
+
+// Tissue mechanisms in the absorbing layer (two-stage layer, Sec. 4.4 /
+// Sec. 5.4): the strength of every tissue mechanism of a cell at depth s
+// into the layer (cells, largest over the axes, at the cell centre) is
+// r = 1 - (s/L_r)^2 for s < L_r, 0 beyond, at a fixed relaxation rate:
+// a -> r a, b unchanged, so ceff -> 1/kappa + r (ceff - 1/kappa).
+template <typename R>
+__device__ __forceinline__ R layer_depth(int c, int n, int w)
+{
+    if (n <= 1 || w <= 0) return R(0);
+    return fmax(R(0), fmax(R(w) - R(0.5) - R(c), R(c) - (R(n - w) - R(0.5))));
+}
+
+template <typename R>
+__device__ __forceinline__ R ramp_of(R s, R inv_lr)
+{
+    if (s <= R(0)) return R(1);
+    const R q = s * inv_lr;
+    return q < R(1) ? R(1) - q * q : R(0);
+}
 
 template <typename R, typename SS, typename SP> struct VelArgs {
     Geo<R> g;
@@ -405,9 +426,15 @@ k_velocity(const VelArgs<R, SS, SP> A)
 #pragma unroll
         for (int e = 0; e < 4; ++e) { pdx[e] = A.pd[0][x0 + e]; pax[e] = A.pa[0][x0 + e]; }
     if (pml_y && hd) { pdy = A.pd[1][y]; pay = A.pa[1][y]; }
+    // layer depths of this thread's cells along x and y (fixed over the march)
+    R sxy[4] = {R(0), R(0), R(0), R(0)};
+    const R inv_lr = G.wabs > 0 ? R(1) / G.lr : R(0);
+    if ((pml_x || pml_y) && hd)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) sxy[e] = fmax(layer_depth<R>(x0 + e, G.nx, G.wabs), layer_depth<R>(y, G.ny, G.wabs));
     // class coefficients of the last class seen (classes rarely change along a column)
     int ccls = -1;
-    R hdr[4], A1[4], B1[4], H1[4];
+    R hdr[4], A1[4], B1[4], H1[4], ik1 = R(1);
 
     for (int k = z0; k < z1; ++k) {
         const long long pk = (long long)k * G.plane;
@@ -478,6 +505,13 @@ k_velocity(const VelArgs<R, SS, SP> A)
             const uint2 cl = *reinterpret_cast<const uint2 *>(reinterpret_cast<const uint16_t *>(st + L::o_cls) + e0);
             const uint16_t cls4[4] = {(uint16_t)(cl.x & 0xffffu), (uint16_t)(cl.x >> 16),
                                       (uint16_t)(cl.y & 0xffffu), (uint16_t)(cl.y >> 16)};
+            // tissue-mechanism strength of the four cells (1 outside the layer)
+            R rr[4] = {R(1), R(1), R(1), R(1)};
+            if (pml_x || pml_y || pml_z) {
+                const R sz = layer_depth<R>(k, G.nz, G.wabs);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) rr[e] = ramp_of(fmax(sxy[e], sz), inv_lr);
+            }
             // one direction at a time: its v and psi come from the stage
 #pragma unroll
             for (int ax = 0; ax < 3; ++ax) {
@@ -498,16 +532,20 @@ k_velocity(const VelArgs<R, SS, SP> A)
                         lut4(A.lut, c, kLutA1, A1);
                         lut4(A.lut, c, kLutB1, B1);
                         lut4(A.lut, c, kLutH1, H1);
+                        ik1 = fw_rcp(hdr[0]);
                         ccls = c;
                     }
                     const bool live = x0 + e < G.nx;
                     const R gd = g[ax][e];
-                    R stv = gd * hdr[2];
+                    // ramped cell: ceff = 1/kappa + r sum a/2, drive r g
+                    const R ce = rr[e] == R(1) ? hdr[2] : ik1 + rr[e] * (hdr[2] - ik1);
+                    const R rg = rr[e] * gd;
+                    R stv = gd * ce;
 #pragma unroll
                     for (int m = 0; m < NM; ++m) {
                         const R po = ps[m][e];
                         stv += H1[m] * po;
-                        ps[m][e] = live ? B1[m] * po + A1[m] * gd : R(0);
+                        ps[m][e] = live ? B1[m] * po + A1[m] * rg : R(0);
                     }
                     if (pml_here) {
                         const R d = ax == 0 ? pdx[e] : (ax == 1 ? pdy : pdz);
@@ -628,8 +666,13 @@ k_pressure(const PresArgs<R, SS, SP> A)
 #pragma unroll
         for (int e = 0; e < 4; ++e) { pdx[e] = A.pd[0][x0 + e]; pax[e] = A.pa[0][x0 + e]; }
     if (pml_y && hd) { pdy = A.pd[1][y]; pay = A.pa[1][y]; }
+    R sxy[4] = {R(0), R(0), R(0), R(0)};
+    const R inv_lr = G.wabs > 0 ? R(1) / G.lr : R(0);
+    if ((pml_x || pml_y) && hd)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) sxy[e] = fmax(layer_depth<R>(x0 + e, G.nx, G.wabs), layer_depth<R>(y, G.ny, G.wabs));
     int ccls = -1;
-    R hdr[4], A2[4], B2[4], H2[4];
+    R hdr[4], A2[4], B2[4], H2[4], ik2 = R(1);
     for (int k = z0; k < z1; ++k) {
         const long long pk = (long long)k * G.plane;
         const int buf = k & 1;
@@ -688,6 +731,12 @@ k_pressure(const PresArgs<R, SS, SP> A)
                 const bool pml_here = ax == 0 ? pml_x : (ax == 1 ? pml_y : pml_z);
                 if (pml_here) Sm<SS>::ld(reinterpret_cast<const SS *>(st + L::o_pml) + ax * L::TILE + e0, pp[ax]);
             }
+            R rr[4] = {R(1), R(1), R(1), R(1)};
+            if (pml_x || pml_y || pml_z) {
+                const R sz = layer_depth<R>(k, G.nz, G.wabs);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) rr[e] = ramp_of(fmax(sxy[e], sz), inv_lr);
+            }
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int c = cls4[e];
@@ -696,17 +745,20 @@ k_pressure(const PresArgs<R, SS, SP> A)
                     lut4(A.lut, c, kLutA2, A2);
                     lut4(A.lut, c, kLutB2, B2);
                     lut4(A.lut, c, kLutH2, H2);
+                    ik2 = fw_rcp(hdr[1]);
                     ccls = c;
                 }
                 const bool live = x0 + e < G.nx;
                 R div = qd[0][e] + qd[2][e];
                 if (DIM == 3) div += qd[1][e];
-                R stp = div * hdr[3];
+                const R ce = rr[e] == R(1) ? hdr[3] : ik2 + rr[e] * (hdr[3] - ik2);
+                const R rdiv = rr[e] * div;
+                R stp = div * ce;
 #pragma unroll
                 for (int m = 0; m < NM; ++m) {
                     const R po = ps[m][e];
                     stp += H2[m] * po;
-                    ps[m][e] = live ? B2[m] * po + A2[m] * div : R(0);
+                    ps[m][e] = live ? B2[m] * po + A2[m] * rdiv : R(0);
                 }
 #pragma unroll
                 for (int ax = 0; ax < 3; ++ax) {
@@ -761,23 +813,40 @@ k_pressure(const PresArgs<R, SS, SP> A)
 
 template <typename SS, typename R>
 __global__ void k_sources(SS *p, const long long *idx, const R *gain, const int *wave_of,
-                          const R *waves, int wave_len, int n_src, const int *d_it, int j)
+                          const R *waves, int wave_len, int n_src, const int *d_it, int j, long long vol,
+                          Monitor *mon)
 {
     const int it = *d_it + j;
     if (it >= wave_len) return;
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n_src; s += gridDim.x * blockDim.x)
-        p[idx[s]] = SS(R(p[idx[s]]) + gain[s] * waves[(size_t)wave_of[s] * wave_len + it]);
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n_src; s += gridDim.x * blockDim.x) {
+        const long long k = idx[s];
+        if (it < 0 || k < 0 || k >= vol) {     // never for a consistent medium: record, skip
+            atomicExch(&mon->bad_index, 1);
+            continue;
+        }
+        p[k] = SS(R(p[k]) + gain[s] * waves[(size_t)wave_of[s] * wave_len + it]);
+    }
 }
 
 template <typename SS>
 __global__ void k_receivers(const SS *p, const long long *idx, SS *traces, int n_rcv, int n_rec,
-                            int decim, const int *d_it, int j)
+                            int decim, const int *d_it, int j, long long vol, Monitor *mon)
 {
     const int it = *d_it + j;
+    if (it < 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&mon->bad_index, 1);
+        return;
+    }
     if (it % decim != 0 || it / decim >= n_rec) return;
     const int col = it / decim;
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n_rcv; r += gridDim.x * blockDim.x)
-        traces[(size_t)r * n_rec + col] = p[idx[r]];
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n_rcv; r += gridDim.x * blockDim.x) {
+        const long long k = idx[r];
+        if (k < 0 || k >= vol) {
+            atomicExch(&mon->bad_index, 1);
+            continue;
+        }
+        traces[(size_t)r * n_rec + col] = p[k];
+    }
 }
 
 __global__ void k_advance(int *d_it, int n);

@@ -37,6 +37,7 @@ template <typename R> Geo<R> make_geo(const fw_medium *m)
     g.c3 = R(cm[2] / m->dx);
     g.c4 = R(cm[3] / m->dx);
     g.dt = R(m->dt);
+    g.lr = R(m->g.transition > 0 ? m->g.transition : 0.5 * m->g.pml);
     return g;
 }
 
@@ -126,13 +127,13 @@ cudaError_t launch_io(const fw_medium *m, int j, cudaStream_t s)
         k_sources<SS, R><<<nb, 256, 0, s>>>(static_cast<SS *>(m->p), m->src_idx,
                                             static_cast<const R *>(m->src_gain), m->wave_of,
                                             static_cast<const R *>(m->waves), m->wave_len, m->n_src,
-                                            m->d_it, j);
+                                            m->d_it, j, (long long)m->vol, m->mon);
     }
     if (m->n_rcv > 0) {
         int nb = (m->n_rcv + 255) / 256;
         k_receivers<SS><<<nb, 256, 0, s>>>(static_cast<const SS *>(m->p), m->rcv_idx,
                                            static_cast<SS *>(m->traces), m->n_rcv, m->n_rec,
-                                           m->decim, m->d_it, j);
+                                           m->decim, m->d_it, j, (long long)m->vol, m->mon);
     }
     return cudaGetLastError();
 }
