@@ -328,6 +328,100 @@ int fw_medium_get_info(fw_medium *m, fw_medium_info *info);
 /* Release the medium and all its device memory (NULL is ignored). */
 void fw_destroy_medium(fw_medium *m);
 
+/* ---- serving: continuous batching of simulation requests ---------------
+ * No counterpart in the paper (it runs one simulation at a time).  A server
+ * owns one device arena of opts.hbm_budget bytes and a scheduler thread.
+ * Requests queue in arrival order; one is admitted as soon as a slot is free
+ * and its footprint (fw_medium_bytes plus source/receiver buffers and the
+ * upload staging) fits in what the arena has left (first fit in arrival
+ * order; a queued request skipped FW_SERVER_MAX_SKIPS times blocks the ones
+ * behind it until it fits).  Admitted media are built by a worker thread
+ * from the request's maps, stay resident on the device, and advance in
+ * chunks of opts.chunk_steps steps through their cached CUDA graphs
+ * (fw_run), each request on a stream of a pool, at most two chunks in
+ * flight per request, so the work of all admitted requests overlaps on the
+ * GPU.  A finished request's traces are copied to its traces_out, its
+ * medium is released into the arena, and the next request is admitted.
+ * Kernels are deterministic: a request's result does not depend on what
+ * else is admitted.  Times are seconds on the server's clock (fw_server_now).
+ * FWGB_SERVER_DEBUG=1 in the environment logs builds and failed chunks to
+ * stderr. */
+#define FW_SERVER_MAX_SKIPS 8
+#define FW_CANCELLED (-8)        /* completion status of a cancelled request */
+
+typedef struct fw_server fw_server;
+
+typedef struct fw_server_opts {
+    size_t hbm_budget;   /* device arena [bytes]; requests larger are refused (FW_ERR_NOMEM) */
+    int max_active;      /* admitted requests at once (slots), >= 1                           */
+    int chunk_steps;     /* time steps per scheduling quantum, >= 1 (32 = one cached graph)   */
+    int n_streams;       /* device streams the quanta are spread over, >= 1                   */
+} fw_server_opts;
+
+/* One simulation request.  Every pointer must stay valid until the request
+ * completes (its completion record has been returned by fw_server_poll).
+ * Maps and masks as for fw_create_medium_classes / fw_set_sources /
+ * fw_set_receivers; traces_out (host or device, float, [n_rcv][n_rec],
+ * n_rec = ceil(n_steps / decim)) receives the traces at completion. */
+typedef struct fw_request {
+    fw_grid grid;
+    const float *c, *rho, *beta;
+    const uint16_t *class_idx;
+    const fw_relax_params *classes;
+    int n_classes;
+    int storage;                 /* FW_STORE_F32, BF16 or F16                      */
+    const uint8_t *src_mask;
+    const float *waveforms;
+    int n_wave;
+    const int32_t *wave_of;
+    const uint8_t *rcv_mask;
+    int decim;
+    int n_steps;
+    float *traces_out;
+    long long tag;               /* caller's label, returned in the completion      */
+} fw_request;
+
+typedef struct fw_completion {
+    long long id, tag;
+    int status;                  /* FW_OK, FW_ERR_UNSTABLE, FW_CANCELLED, or the error of
+                                    building the medium (FW_ERR_ARG, FW_ERR_NOMEM, ...)  */
+    double t_submit, t_admit, t_done;   /* server clock [s]; t_admit < 0 if never admitted */
+    long long voxel_steps;       /* voxels x steps advanced                               */
+    float max_abs_p;
+} fw_completion;
+
+typedef struct fw_server_stats {
+    int queued, building, active, done;
+    size_t bytes_reserved, bytes_budget, bytes_largest_free;
+} fw_server_stats;
+
+/* Create a server on the current device (its arena is allocated here with
+ * cudaMalloc).  Errors: FW_ERR_ARG, FW_ERR_NOMEM, FW_ERR_CUDA. */
+int fw_server_create(const fw_server_opts *opts, fw_server **out);
+
+/* Queue a request; *id (may be NULL) receives its id.  Never blocks on the
+ * GPU.  A request whose footprint exceeds the whole budget completes at once
+ * with FW_ERR_NOMEM.  Errors: FW_ERR_ARG (bad request fields). */
+int fw_server_submit(fw_server *s, const fw_request *req, long long *id);
+
+/* Wait up to timeout_s seconds (0: do not wait) for completions and copy up
+ * to max of them into out; *n receives how many.  Each completion is
+ * returned once. */
+int fw_server_poll(fw_server *s, fw_completion *out, int max, int *n, double timeout_s);
+
+/* Cancel a queued or running request (it completes with FW_CANCELLED after
+ * its in-flight chunks end).  FW_ERR_ARG if the id is unknown or done. */
+int fw_server_cancel(fw_server *s, long long id);
+
+int fw_server_stats_get(fw_server *s, fw_server_stats *st);
+
+/* Seconds on the server's clock (zero at creation). */
+double fw_server_now(fw_server *s);
+
+/* Cancel what is queued, let running requests end their in-flight chunks,
+ * release everything.  NULL is ignored. */
+void fw_server_destroy(fw_server *s);
+
 const char *fw_strerror(int code);
 
 /* Library version: major*10000 + minor*100 + patch. */

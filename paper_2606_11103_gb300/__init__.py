@@ -295,3 +295,94 @@ class Medium:
             self.close()
         except Exception:  # noqa: BLE001
             pass
+
+
+# ---------------------------------------------------------------------------
+# serving
+
+
+class Server:
+    """Owner of one ``fw_server*`` (continuous batching of simulation
+    requests on the current device).  ``submit`` keeps the request's buffers
+    alive until its completion has been polled."""
+
+    def __init__(self, hbm_budget, max_active=8, chunk_steps=32, n_streams=8):
+        o = _lib.fw_server_opts()
+        o.hbm_budget, o.max_active, o.chunk_steps, o.n_streams = int(hbm_budget), int(max_active), \
+            int(chunk_steps), int(n_streams)
+        self.h = C.c_void_p()
+        check(lib().fw_server_create(C.byref(o), C.byref(self.h)), "fw_server_create")
+        self._keep = {}
+
+    def submit(self, shape, dx, dt, c, rho, class_idx, classes, n_steps, src_mask=None, waves=None, wave_of=None,
+               rcv_mask=None, decim=1, beta=None, pml=0, transition=0, f0=3e6, storage="f32", traces_out=None,
+               tag=0):
+        """Queue one request; returns (id, traces_out).  traces_out (numpy or
+        torch, float32 [n_rcv, n_rec]) is filled at completion."""
+        r = _lib.fw_request()
+        r.grid = make_grid(shape, dx, dt, 0.0, pml, transition, f0)
+        keep = [_Buf(c, np.float32), _Buf(rho, np.float32), _Buf(class_idx, np.uint16)]
+        r.c, r.rho, r.class_idx = keep[0].ptr, keep[1].ptr, keep[2].ptr
+        if beta is not None:
+            keep.append(_Buf(beta, np.float32))
+            r.beta = keep[-1].ptr
+        arr = (fw_relax_params * len(classes))(*classes)
+        keep.append(arr)
+        r.classes, r.n_classes = arr, len(classes)
+        r.storage = STORAGE.get(storage, storage)
+        n_rcv = 0
+        if src_mask is not None:
+            w = np.ascontiguousarray(np.atleast_2d(waves), dtype=np.float32)
+            keep += [_Buf(src_mask, np.uint8), w]
+            r.src_mask, r.waveforms, r.n_wave = keep[-2].ptr, C.c_void_p(w.ctypes.data), w.shape[0]
+            if wave_of is not None:
+                keep.append(_Buf(wave_of, np.int32))
+                r.wave_of = keep[-1].ptr
+        if rcv_mask is not None:
+            keep.append(_Buf(rcv_mask, np.uint8))
+            r.rcv_mask = keep[-1].ptr
+            n_rcv = int(np.count_nonzero(np.asarray(rcv_mask.cpu() if hasattr(rcv_mask, "cpu") else rcv_mask)))
+        r.decim, r.n_steps, r.tag = int(decim), int(n_steps), int(tag)
+        if traces_out is None and n_rcv:
+            traces_out = np.zeros((n_rcv, (n_steps + decim - 1) // decim), np.float32)
+        if traces_out is not None:
+            r.traces_out = C.c_void_p(traces_out.data_ptr() if hasattr(traces_out, "data_ptr")
+                                      else traces_out.ctypes.data)
+        rid = C.c_longlong()
+        check(lib().fw_server_submit(self.h, C.byref(r), C.byref(rid)), "fw_server_submit")
+        self._keep[rid.value] = (r, keep, traces_out)
+        return rid.value, traces_out
+
+    def poll(self, timeout=0.0, max_n=256):
+        """Completed requests as dicts (each returned once)."""
+        out = (_lib.fw_completion * max_n)()
+        n = C.c_int()
+        check(lib().fw_server_poll(self.h, out, max_n, C.byref(n), float(timeout)), "fw_server_poll")
+        res = []
+        for k in range(n.value):
+            d = {f: getattr(out[k], f) for f, _ in _lib.fw_completion._fields_}
+            d["traces"] = self._keep.pop(d["id"], (None, None, None))[2]
+            res.append(d)
+        return res
+
+    def cancel(self, rid):
+        check(lib().fw_server_cancel(self.h, C.c_longlong(rid)), "fw_server_cancel")
+
+    def stats(self):
+        st = _lib.fw_server_stats()
+        check(lib().fw_server_stats_get(self.h, C.byref(st)), "fw_server_stats_get")
+        return {f: getattr(st, f) for f, _ in _lib.fw_server_stats._fields_}
+
+    def now(self):
+        return lib().fw_server_now(self.h)
+
+    def close(self):
+        if self.h:
+            lib().fw_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass

@@ -18,6 +18,8 @@ FW_ERR_UNSTABLE = -4
 FW_ERR_STATE = -5
 FW_ERR_UNSUPPORTED = -6
 FW_ERR_SIZE = -7
+FW_CANCELLED = -8
+FW_SERVER_MAX_SKIPS = 8
 FW_NOALLOC_MAX_BYTES = 64 << 20
 
 FW_STORE_F32, FW_STORE_BF16, FW_STORE_F16, FW_STORE_F64 = 0, 1, 2, 3
@@ -53,6 +55,30 @@ class fw_medium_info(C.Structure):
                 ("dx", C.c_double), ("dt", C.c_double), ("c_max", C.c_double), ("ceff_max", C.c_double),
                 ("device_bytes", C.c_size_t), ("step", C.c_longlong),
                 ("n_src", C.c_int), ("n_rcv", C.c_int), ("n_rec", C.c_int)]
+
+
+class fw_server_opts(C.Structure):
+    _fields_ = [("hbm_budget", C.c_size_t), ("max_active", C.c_int), ("chunk_steps", C.c_int),
+                ("n_streams", C.c_int)]
+
+
+class fw_request(C.Structure):
+    _fields_ = [("grid", fw_grid), ("c", C.c_void_p), ("rho", C.c_void_p), ("beta", C.c_void_p),
+                ("class_idx", C.c_void_p), ("classes", C.POINTER(fw_relax_params)), ("n_classes", C.c_int),
+                ("storage", C.c_int), ("src_mask", C.c_void_p), ("waveforms", C.c_void_p), ("n_wave", C.c_int),
+                ("wave_of", C.c_void_p), ("rcv_mask", C.c_void_p), ("decim", C.c_int), ("n_steps", C.c_int),
+                ("traces_out", C.c_void_p), ("tag", C.c_longlong)]
+
+
+class fw_completion(C.Structure):
+    _fields_ = [("id", C.c_longlong), ("tag", C.c_longlong), ("status", C.c_int), ("t_submit", C.c_double),
+                ("t_admit", C.c_double), ("t_done", C.c_double), ("voxel_steps", C.c_longlong),
+                ("max_abs_p", C.c_float)]
+
+
+class fw_server_stats(C.Structure):
+    _fields_ = [("queued", C.c_int), ("building", C.c_int), ("active", C.c_int), ("done", C.c_int),
+                ("bytes_reserved", C.c_size_t), ("bytes_budget", C.c_size_t), ("bytes_largest_free", C.c_size_t)]
 
 
 OBJFN = C.CFUNCTYPE(C.c_double, C.POINTER(C.c_double), C.c_void_p)
@@ -96,6 +122,13 @@ SIGNATURES = {
     "fw_status": (_I, [_P, C.POINTER(C.c_float)]),
     "fw_medium_get_info": (_I, [_P, C.POINTER(fw_medium_info)]),
     "fw_destroy_medium": (None, [_P]),
+    "fw_server_create": (_I, [C.POINTER(fw_server_opts), C.POINTER(_P)]),
+    "fw_server_submit": (_I, [_P, C.POINTER(fw_request), C.POINTER(C.c_longlong)]),
+    "fw_server_poll": (_I, [_P, C.POINTER(fw_completion), _I, C.POINTER(_I), C.c_double]),
+    "fw_server_cancel": (_I, [_P, C.c_longlong]),
+    "fw_server_stats_get": (_I, [_P, C.POINTER(fw_server_stats)]),
+    "fw_server_now": (C.c_double, [_P]),
+    "fw_server_destroy": (None, [_P]),
     "fw_strerror": (C.c_char_p, [_I]),
     "fw_version": (_I, []),
 }

@@ -39,10 +39,20 @@ void *(*g_alloc)(size_t, void *) = nullptr;
 void (*g_free)(void *, void *) = nullptr;
 void *g_alloc_ctx = nullptr;
 
+// a per-thread allocator (the serving runtime's device arena) takes
+// precedence over the process-wide hook
+struct ThreadHook {
+    void *(*alloc)(size_t, void *) = nullptr;
+    void (*release)(void *, void *) = nullptr;
+    void *ctx = nullptr;
+};
+thread_local ThreadHook t_hook;
+
 void *dev_alloc(size_t bytes)
 {
-    std::lock_guard<std::mutex> lk(g_alloc_mu);
     if (bytes == 0) bytes = 256;
+    if (t_hook.alloc) return t_hook.alloc(bytes, t_hook.ctx);
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
     if (g_alloc) return g_alloc(bytes, g_alloc_ctx);
     void *p = nullptr;
     if (cudaMalloc(&p, bytes) != cudaSuccess) {
@@ -55,6 +65,10 @@ void *dev_alloc(size_t bytes)
 void dev_free(void *p)
 {
     if (!p) return;
+    if (t_hook.release) {
+        t_hook.release(p, t_hook.ctx);
+        return;
+    }
     std::lock_guard<std::mutex> lk(g_alloc_mu);
     if (g_free) g_free(p, g_alloc_ctx);
     else cudaFree(p);
@@ -709,6 +723,12 @@ namespace fwgb {
 // device memory through the installed allocator, and the size of the state
 // image (the checkpoint image without the step counter), for the adjoint
 void *device_alloc(size_t bytes) { return dev_alloc(bytes); }
+void set_thread_allocator(void *(*alloc)(size_t, void *), void (*release)(void *, void *), void *ctx)
+{
+    t_hook.alloc = alloc;
+    t_hook.release = release;
+    t_hook.ctx = ctx;
+}
 void device_free(void *p) { dev_free(p); }
 size_t state_image_bytes(const fw_medium *m)
 {
