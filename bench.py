@@ -48,6 +48,11 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=0, help="streaming end-to-end steps (0: = --steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--workload", default="voronoi3d", choices=["voronoi3d", "serving"],
+                    help="serving: the mixed 2D/3D request stream through the continuous-batching server")
+    ap.add_argument("--requests", type=int, default=40, help="serving: requests in the stream (200 = full mix)")
+    ap.add_argument("--slots", type=int, default=8, help="serving: admitted requests at once")
+    ap.add_argument("--load", type=float, default=0.8, help="serving: offered load / one-at-a-time capacity")
     return ap.parse_args()
 
 
@@ -420,10 +425,137 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# serving: continuous batching vs one request at a time
+
+
+def _serving_arm(fw, media, classes, arrivals, budget, slots, streams, chunk=32):
+    """Replay the arrival stream through one server; returns per-request
+    completions (tag -> dict) and the server-clock origin."""
+    from synthetic.serving import DT, DX, F0, PML
+    srv = fw.Server(budget, max_active=slots, chunk_steps=chunk, n_streams=streams)
+    t0 = srv.now()
+    done, i, n = {}, 0, len(media)
+    last = time.perf_counter()
+    while len(done) < n:
+        now = srv.now() - t0
+        while i < n and arrivals[i] <= now:
+            q = media[i]
+            srv.submit(q["shape"], DX, DT, q["c"], q["rho"], q["class_idx"], classes[i], q["n_steps"],
+                       src_mask=q["src_mask"], waves=q["waves"], rcv_mask=q["rcv_mask"], pml=PML, f0=F0, tag=i)
+            i += 1
+        wait = (arrivals[i] - (srv.now() - t0)) if i < n else 0.5
+        for d in srv.poll(timeout=max(0.0, min(wait, 0.5))):
+            done[d["tag"]] = d
+            last = time.perf_counter()
+            if d["status"] != 0:
+                log("  request %d %s: status %d" % (d["tag"], media[d["tag"]]["shape"], d["status"]))
+        if time.perf_counter() - last > 300 and i == n:
+            log("serving: no completion for 300 s, stats %s" % srv.stats())
+            srv.close()
+            raise RuntimeError("serving arm stalled")
+    srv.close()
+    return done, t0
+
+
+def _arm_summary(done, t0, arrivals):
+    lat = np.array([done[k]["t_done"] - done[k]["t_submit"] for k in sorted(done)])
+    wait = np.array([done[k]["t_admit"] - done[k]["t_submit"] for k in sorted(done)])
+    vs = sum(d["voxel_steps"] for d in done.values())
+    span = max(d["t_done"] for d in done.values()) - (t0 + float(arrivals[0]))
+    bad = {int(k): int(d["status"]) for k, d in done.items() if d["status"] != 0}
+    return {"value": round(vs / span / 1e9, 3), "unit": "Gvoxel-updates/s", "makespan_s": round(span, 2),
+            "p50_s": round(float(np.percentile(lat, 50)), 3), "p99_s": round(float(np.percentile(lat, 99)), 3),
+            "mean_queue_s": round(float(wait.mean()), 3), "failed": bad}
+
+
+def run_serving(args):
+    """Mixed stream of 2D (512^2-4096^2) and 3D (128^3-384^3) requests with
+    500-3000 steps (Poisson arrivals at args.load of the measured
+    one-at-a-time capacity) through the continuous-batching server and
+    through the same server limited to one request at a time; then the same
+    stream submitted at once (capacity)."""
+    import torch
+    torch.cuda.set_device(0)
+    import paper_2606_11103_gb300 as fw
+    from paper_2606_11103_gb300 import build as fwbuild
+    from synthetic import serving_stream
+    from synthetic.serving import DT, DX, F0, PML, lut_pairs, request_media
+    fwbuild.build()
+    pairs = lut_pairs()
+    lut = [None] * len(pairs)
+
+    def job(k):
+        lut[k], _ = fw.fit_relaxation(pairs[k][0], pairs[k][1], 4, maxiter=3000, w=(0.1, 0.5, 0.9))
+
+    t0 = time.perf_counter()
+    th = [threading.Thread(target=job, args=(k,)) for k in range(len(pairs))]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    t_fit = time.perf_counter() - t0
+    reqs = serving_stream(seed=3, n_req=args.requests, rate_hz=1.0)
+    t0 = time.perf_counter()
+    media = [request_media(r, len(pairs)) for r in reqs]
+    torch.cuda.synchronize()
+    classes = [[lut[k] for k in q["lut_idx"]] for q in media]
+    log("serving: %d table pairs fitted in %.1fs, %d requests generated in %.1fs" %
+        (len(pairs), t_fit, len(reqs), time.perf_counter() - t0))
+    # one-at-a-time service rate per dimension, from one request of each
+    rate = {}
+    for nd in (2, 3):
+        k = next(i for i, q in enumerate(media) if len(q["shape"]) == nd)
+        q = media[k]
+        m = fw.Medium.from_classes(q["shape"], DX, q["c"], q["rho"], q["class_idx"], classes[k], dt=DT, pml=PML, f0=F0)
+        n = min(300, q["n_steps"])
+        m.run(32)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        m.run(n)
+        torch.cuda.synchronize()
+        rate[nd] = int(np.prod(q["shape"])) * n / (time.perf_counter() - t1)
+        m.close()
+    work = np.array([int(np.prod(q["shape"])) * q["n_steps"] for q in media], np.float64)
+    service = np.array([w / rate[len(q["shape"])] for w, q in zip(work, media)])
+    lam = args.load / service.mean()
+    gaps = np.diff([r["arrival"] for r in reqs], prepend=0.0)       # seeded Exp(1) gaps
+    arrivals = np.cumsum(gaps) / lam
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(min(200e9, 0.8 * free))
+    with ClockSampler(0) as clk:
+        batched, tb = _serving_arm(fw, media, classes, arrivals, budget, args.slots, args.slots)
+    single, ts = _serving_arm(fw, media, classes, arrivals, budget, 1, 1)
+    same = sum(int(batched[k]["status"] == 0 and np.array_equal(batched[k]["traces"], single[k]["traces"]))
+               for k in batched)
+    sb, ss = _arm_summary(batched, tb, arrivals), _arm_summary(single, ts, arrivals)
+    zero = np.zeros(len(media))
+    cap_b, tcb = _serving_arm(fw, media, classes, zero, budget, args.slots, args.slots)
+    cap_s, tcs = _serving_arm(fw, media, classes, zero, budget, 1, 1)
+    cb, cs = _arm_summary(cap_b, tcb, zero), _arm_summary(cap_s, tcs, zero)
+    out = {
+        "metric": "serving throughput, mixed 2D/3D request stream", "value": cb["value"], "unit": "Gvoxel-updates/s",
+        "higher_is_better": True, "p50_s": sb["p50_s"], "p99_s": sb["p99_s"],
+        "capacity": {"batched": cb, "one_at_a_time": cs},
+        "at_offered_load": {"batched": sb, "one_at_a_time": ss},
+        "n_requests": len(media), "identical_results": "%d/%d" % (same, len(media)),
+        "offered_load": args.load, "service_rate_gvox_s": {"2d": round(rate[2] / 1e9, 2), "3d": round(rate[3] / 1e9, 2)},
+        "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "Poisson stream (seed 3) of %d requests: 2D 512^2-4096^2, 3D 128^3-384^3 Voronoi "
+                               "media (8 classes from a 36-pair table, N=4), 500-3000 steps" % len(media),
+                   "slots": args.slots, "streams": args.slots, "chunk_steps": 32, "hbm_budget_gb": round(budget / 1e9, 1),
+                   "arrival_span_s": round(float(arrivals[-1]), 2)},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 
