@@ -26,8 +26,6 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include <type_traits>
-
 #include "fw_internal.h"
 
 namespace fwgb {
@@ -507,17 +505,14 @@ k_velocity(const VelArgs<R, SS, SP> A)
             const uint2 cl = *reinterpret_cast<const uint2 *>(reinterpret_cast<const uint16_t *>(st + L::o_cls) + e0);
             const uint16_t cls4[4] = {(uint16_t)(cl.x & 0xffffu), (uint16_t)(cl.x >> 16),
                                       (uint16_t)(cl.y & 0xffffu), (uint16_t)(cl.y >> 16)};
-            // one direction at a time: its v and psi come from the stage.
-            // Threads with cells in the absorbing layer take the tissue ramp;
-            // the others run the plain update as its own instruction stream.
-            auto directions = [&](auto ramped) {
-            constexpr bool RAMP = decltype(ramped)::value;
+            // tissue-mechanism strength of the four cells (1 outside the layer)
             R rr[4] = {R(1), R(1), R(1), R(1)};
-            if (RAMP) {
+            if (pml_x || pml_y || pml_z) {
                 const R sz = layer_depth<R>(k, G.nz, G.wabs);
 #pragma unroll
                 for (int e = 0; e < 4; ++e) rr[e] = ramp_of(fmax(sxy[e], sz), inv_lr);
             }
+            // one direction at a time: its v and psi come from the stage
 #pragma unroll
             for (int ax = 0; ax < 3; ++ax) {
                 if (DIM == 2 && ax == 1) continue;
@@ -543,11 +538,8 @@ k_velocity(const VelArgs<R, SS, SP> A)
                     const bool live = x0 + e < G.nx;
                     const R gd = g[ax][e];
                     // ramped cell: ceff = 1/kappa + r sum a/2, drive r g
-                    R ce = hdr[2], rg = gd;
-                    if (RAMP && rr[e] != R(1)) {
-                        ce = ik1 + rr[e] * (hdr[2] - ik1);
-                        rg = rr[e] * gd;
-                    }
+                    const R ce = rr[e] == R(1) ? hdr[2] : ik1 + rr[e] * (hdr[2] - ik1);
+                    const R rg = rr[e] * gd;
                     R stv = gd * ce;
 #pragma unroll
                     for (int m = 0; m < NM; ++m) {
@@ -572,9 +564,6 @@ k_velocity(const VelArgs<R, SS, SP> A)
                 for (int m = 0; m < NM; ++m) Io<SP>::st(A.psi[m][ax] + pk + row, ps[m]);
                 if (pml_here) Io<SS>::st(A.psip[ax] + pk + row, pp);
             }
-            };
-            if (pml_x || pml_y || pml_z) directions(std::true_type{});
-            else directions(std::false_type{});
         }
 #pragma unroll
         for (int j = 0; j < 7; ++j)
@@ -742,12 +731,8 @@ k_pressure(const PresArgs<R, SS, SP> A)
                 const bool pml_here = ax == 0 ? pml_x : (ax == 1 ? pml_y : pml_z);
                 if (pml_here) Sm<SS>::ld(reinterpret_cast<const SS *>(st + L::o_pml) + ax * L::TILE + e0, pp[ax]);
             }
-            // as in the velocity sweep: layer threads take the tissue ramp,
-            // the others the plain update
-            auto points = [&](auto ramped) {
-            constexpr bool RAMP = decltype(ramped)::value;
             R rr[4] = {R(1), R(1), R(1), R(1)};
-            if (RAMP) {
+            if (pml_x || pml_y || pml_z) {
                 const R sz = layer_depth<R>(k, G.nz, G.wabs);
 #pragma unroll
                 for (int e = 0; e < 4; ++e) rr[e] = ramp_of(fmax(sxy[e], sz), inv_lr);
@@ -766,11 +751,8 @@ k_pressure(const PresArgs<R, SS, SP> A)
                 const bool live = x0 + e < G.nx;
                 R div = qd[0][e] + qd[2][e];
                 if (DIM == 3) div += qd[1][e];
-                R ce = hdr[3], rdiv = div;
-                if (RAMP && rr[e] != R(1)) {
-                    ce = ik2 + rr[e] * (hdr[3] - ik2);
-                    rdiv = rr[e] * div;
-                }
+                const R ce = rr[e] == R(1) ? hdr[3] : ik2 + rr[e] * (hdr[3] - ik2);
+                const R rdiv = rr[e] * div;
                 R stp = div * ce;
 #pragma unroll
                 for (int m = 0; m < NM; ++m) {
@@ -800,9 +782,6 @@ k_pressure(const PresArgs<R, SS, SP> A)
                 bad |= !(ap <= R(3.0e38));
                 pmax = fmax(pmax, ap);
             }
-            };
-            if (pml_x || pml_y || pml_z) points(std::true_type{});
-            else points(std::false_type{});
             Io<SS>::st(A.p + pk + row, pv);
 #pragma unroll
             for (int m = 0; m < NM; ++m) Io<SP>::st(A.psi[m] + pk + row, ps[m]);
