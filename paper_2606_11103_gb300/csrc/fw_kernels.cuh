@@ -390,7 +390,7 @@ __device__ __forceinline__ void vel_issue(const VelArgs<R, SS, SP> &A, unsigned 
 }
 
 template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY>
-__global__ void __launch_bounds__(BX *BY, (DIM == 3 && BY < 8) ? 2 : 1)
+__global__ void __launch_bounds__(BX *BY, DIM == 3 ? (BY < 8 ? 3 : 2) : 1)
 k_velocity(const VelArgs<R, SS, SP> A)
 {
     using L = VelSmem<R, SS, SP, DIM, NM, BX, BY>;
@@ -434,7 +434,7 @@ k_velocity(const VelArgs<R, SS, SP> A)
         for (int e = 0; e < 4; ++e) sxy[e] = fmax(layer_depth<R>(x0 + e, G.nx, G.wabs), layer_depth<R>(y, G.ny, G.wabs));
     // class coefficients of the last class seen (classes rarely change along a column)
     int ccls = -1;
-    R hdr[4], A1[4], B1[4], H1[4], ik1 = R(1);
+    R hdr[4], A1[4], B1[4], H1[4], dk1 = R(0);   // dk1 = ceff1 - 1/kappa1 of the cached class
 
     for (int k = z0; k < z1; ++k) {
         const long long pk = (long long)k * G.plane;
@@ -532,20 +532,21 @@ k_velocity(const VelArgs<R, SS, SP> A)
                         lut4(A.lut, c, kLutA1, A1);
                         lut4(A.lut, c, kLutB1, B1);
                         lut4(A.lut, c, kLutH1, H1);
-                        ik1 = fw_rcp(hdr[0]);
+                        dk1 = hdr[2] - fw_rcp(hdr[0]);
                         ccls = c;
                     }
+                    // a dead lane (x >= nx) gets drive 0, so its memory variables stay exactly 0
                     const bool live = x0 + e < G.nx;
-                    const R gd = g[ax][e];
-                    // ramped cell: ceff = 1/kappa + r sum a/2, drive r g
-                    const R ce = rr[e] == R(1) ? hdr[2] : ik1 + rr[e] * (hdr[2] - ik1);
+                    const R gd = live ? g[ax][e] : R(0);
+                    // ramped cell: ceff = 1/kappa + r sum a/2 (exact at r = 1), drive r g
+                    const R ce = hdr[2] + (rr[e] - R(1)) * dk1;
                     const R rg = rr[e] * gd;
                     R stv = gd * ce;
 #pragma unroll
                     for (int m = 0; m < NM; ++m) {
                         const R po = ps[m][e];
                         stv += H1[m] * po;
-                        ps[m][e] = live ? B1[m] * po + A1[m] * rg : R(0);
+                        ps[m][e] = B1[m] * po + A1[m] * rg;
                     }
                     if (pml_here) {
                         const R d = ax == 0 ? pdx[e] : (ax == 1 ? pdy : pdz);
@@ -672,7 +673,7 @@ k_pressure(const PresArgs<R, SS, SP> A)
 #pragma unroll
         for (int e = 0; e < 4; ++e) sxy[e] = fmax(layer_depth<R>(x0 + e, G.nx, G.wabs), layer_depth<R>(y, G.ny, G.wabs));
     int ccls = -1;
-    R hdr[4], A2[4], B2[4], H2[4], ik2 = R(1);
+    R hdr[4], A2[4], B2[4], H2[4], dk2 = R(0);   // dk2 = ceff2 - 1/kappa2 of the cached class
     for (int k = z0; k < z1; ++k) {
         const long long pk = (long long)k * G.plane;
         const int buf = k & 1;
@@ -745,20 +746,21 @@ k_pressure(const PresArgs<R, SS, SP> A)
                     lut4(A.lut, c, kLutA2, A2);
                     lut4(A.lut, c, kLutB2, B2);
                     lut4(A.lut, c, kLutH2, H2);
-                    ik2 = fw_rcp(hdr[1]);
+                    dk2 = hdr[3] - fw_rcp(hdr[1]);
                     ccls = c;
                 }
                 const bool live = x0 + e < G.nx;
                 R div = qd[0][e] + qd[2][e];
                 if (DIM == 3) div += qd[1][e];
-                const R ce = rr[e] == R(1) ? hdr[3] : ik2 + rr[e] * (hdr[3] - ik2);
+                div = live ? div : R(0);       // dead lane: memory variables stay exactly 0
+                const R ce = hdr[3] + (rr[e] - R(1)) * dk2;   // exact at r = 1
                 const R rdiv = rr[e] * div;
                 R stp = div * ce;
 #pragma unroll
                 for (int m = 0; m < NM; ++m) {
                     const R po = ps[m][e];
                     stp += H2[m] * po;
-                    ps[m][e] = live ? B2[m] * po + A2[m] * rdiv : R(0);
+                    ps[m][e] = B2[m] * po + A2[m] * rdiv;
                 }
 #pragma unroll
                 for (int ax = 0; ax < 3; ++ax) {
