@@ -80,6 +80,13 @@ typedef struct fw_grid {
     int transition;    /* L_T cells                                            */
     double f0;         /* centre frequency [Hz] of the absorbing profile       */
     double pml_r0;     /* design reflection of the profile, <= 0 means 1e-5    */
+    int layer_relax;   /* 0: the relaxation classes of the absorbing layer are
+                        * inherited from the nearest interior cell (the adaptive
+                        * layer of Sec. 4.6, the default); 1: the caller's own
+                        * class map (or alpha0, y maps) is kept inside the
+                        * layer, e.g. one fixed class everywhere in it (the
+                        * homogeneous layers of Sec. 4.6).  c, rho and beta
+                        * are inherited either way; other values: FW_ERR_ARG */
 } fw_grid;
 
 /* Relaxation parameters of one class (Sec. 2.1): kappa_x1, kappa_x2 and for

@@ -19,7 +19,7 @@
       d_max = -3 c_max ln(R0) / (2 L_B dx),  R0 = 1e-5,
       alpha(s) = pi f0 (1 - s/(L_T+L_B)),
   and kappa of the mechanism = the tissue kappa of the point's stretch.
-* two-stage layer (Sec. 4.4 methods, Sec. 5.4): the tissue ("higher-order")
+* two-stage layer (Sec. 4.6 methods, Sec. 5.4-5.5): the tissue ("higher-order")
   relaxation mechanisms are ramped across the transition region, and within
   the absorbing region when there is no transition layer, so that the
   absorbing mechanism alone acts at the outer edge.  Reading of the ramp:

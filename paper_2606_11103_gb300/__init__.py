@@ -78,8 +78,10 @@ class _Buf:
         self.ptr = C.c_void_p(arr.ctypes.data)
 
 
-def make_grid(shape, dx, dt=0.0, cfl=0.0, pml=0, transition=0, f0=3e6, pml_r0=0.0) -> fw_grid:
-    """fw_grid from a numpy-order shape (ny, nx) or (nz, ny, nx)."""
+def make_grid(shape, dx, dt=0.0, cfl=0.0, pml=0, transition=0, f0=3e6, pml_r0=0.0, layer_relax=False) -> fw_grid:
+    """fw_grid from a numpy-order shape (ny, nx) or (nz, ny, nx).  layer_relax:
+    keep the caller's relaxation classes inside the absorbing layer instead of
+    inheriting the nearest interior class."""
     g = fw_grid()
     g.ndim = len(shape)
     if g.ndim == 2:
@@ -91,6 +93,7 @@ def make_grid(shape, dx, dt=0.0, cfl=0.0, pml=0, transition=0, f0=3e6, pml_r0=0.
     g.dx, g.dt, g.cfl = float(dx), float(dt), float(cfl)
     g.pml, g.transition = int(pml), int(transition)
     g.f0, g.pml_r0 = float(f0), float(pml_r0)
+    g.layer_relax = int(bool(layer_relax))
     return g
 
 
@@ -174,8 +177,8 @@ class Medium:
     # -- construction ---------------------------------------------------------
     @classmethod
     def from_classes(cls, shape, dx, c, rho, class_idx, classes, dt=0.0, cfl=0.0, beta=None, pml=0,
-                     transition=0, f0=3e6, storage="f32", stream=None):
-        g = make_grid(shape, dx, dt, cfl, pml, transition, f0)
+                     transition=0, f0=3e6, storage="f32", stream=None, layer_relax=False):
+        g = make_grid(shape, dx, dt, cfl, pml, transition, f0, layer_relax=layer_relax)
         arr = (fw_relax_params * len(classes))(*classes)
         bc, br = _Buf(c, np.float32), _Buf(rho, np.float32)
         bb = _Buf(beta, np.float32) if beta is not None else None
@@ -188,8 +191,8 @@ class Medium:
 
     @classmethod
     def from_maps(cls, shape, dx, c, rho, alpha0, y, n_mech=2, dt=0.0, cfl=0.0, beta=None, pml=0,
-                  transition=0, f0=3e6, storage="f32", stream=None, **fit_kw):
-        g = make_grid(shape, dx, dt, cfl, pml, transition, f0)
+                  transition=0, f0=3e6, storage="f32", stream=None, layer_relax=False, **fit_kw):
+        g = make_grid(shape, dx, dt, cfl, pml, transition, f0, layer_relax=layer_relax)
         o = fit_opts(**fit_kw)
         if "c0" not in fit_kw:
             o.c0 = 0.0           # per-class mean sound speed

@@ -29,7 +29,8 @@ FW_FIELD_P, FW_FIELD_V, FW_FIELD_PSI1, FW_FIELD_PSI2, FW_FIELD_PSI1P, FW_FIELD_P
 class fw_grid(C.Structure):
     _fields_ = [("ndim", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
                 ("dx", C.c_double), ("dt", C.c_double), ("cfl", C.c_double),
-                ("pml", C.c_int), ("transition", C.c_int), ("f0", C.c_double), ("pml_r0", C.c_double)]
+                ("pml", C.c_int), ("transition", C.c_int), ("f0", C.c_double), ("pml_r0", C.c_double),
+                ("layer_relax", C.c_int)]
 
 
 class fw_relax_params(C.Structure):

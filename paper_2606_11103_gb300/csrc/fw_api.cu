@@ -280,6 +280,7 @@ int make_dims(const fw_grid *g, int n_mech, int storage, bool nl, Dims *d)
     if (g->nx < 1 || g->ny < 1 || g->nz < 1 || !(g->dx > 0)) return FW_ERR_ARG;
     if (g->ndim == 2 && g->nz != 1) return FW_ERR_ARG;
     if (g->pml < 0 || g->transition < 0 || (g->transition > 0 && g->pml == 0)) return FW_ERR_ARG;
+    if (g->layer_relax != 0 && g->layer_relax != 1) return FW_ERR_ARG;
     d->ndim = g->ndim;
     d->NX = g->nx;
     d->NY = g->ndim == 3 ? g->ny : 1;
@@ -365,9 +366,10 @@ int upload_doubles(fw_medium *m, void *dst, const std::vector<double> &v, cudaSt
 }
 
 // Upload a user map (host or device, dense float) into the padded layout with
-// absorbing-layer inheritance.  T is the device element type.
+// absorbing-layer inheritance (inherit = false: a plain copy, the caller's
+// values kept inside the layer).  T is the device element type.
 template <typename T, typename S>
-int upload_map(const fw_medium *m, T *dst, const S *src, cudaStream_t s)
+int upload_map(const fw_medium *m, T *dst, const S *src, cudaStream_t s, bool inherit = true)
 {
     const size_t n = (size_t)m->NX * m->NY * m->NZ;
     const S *dsrc = src;
@@ -377,7 +379,8 @@ int upload_map(const fw_medium *m, T *dst, const S *src, cudaStream_t s)
         FW_CK(cudaMemcpyAsync(stage.p, src, n * sizeof(S), cudaMemcpyDefault, s));
         dsrc = static_cast<const S *>(stage.p);
     }
-    k_gather_inherit<T, S><<<grid_blocks(n), 256, 0, s>>>(dst, dsrc, m->NX, m->NY, m->NZ, m->px, m->wabs);
+    k_gather_inherit<T, S><<<grid_blocks(n), 256, 0, s>>>(dst, dsrc, m->NX, m->NY, m->NZ, m->px,
+                                                          inherit ? m->wabs : 0);
     FW_CK(cudaGetLastError());
     FW_CK(cudaStreamSynchronize(s));
     return FW_OK;
@@ -620,7 +623,7 @@ int create_common(const fw_grid *g, const float *c, const float *rho, const floa
     } else {
         if ((rc = upload_map(m, (float *)m->cdev, c, s)) || (rc = upload_map(m, (float *)m->rho, rho, s))) { release(m); return rc; }
     }
-    if ((rc = upload_map(m, m->cls, class_idx, s))) { release(m); return rc; }
+    if ((rc = upload_map(m, m->cls, class_idx, s, g->layer_relax == 0))) { release(m); return rc; }
     // c_max and c_eff,max = max c / sqrt(kappa1 kappa2)
     {
         std::vector<double> sc(classes.size());

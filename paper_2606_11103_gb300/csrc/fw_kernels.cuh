@@ -227,7 +227,7 @@ template <typename R> struct Geo {
     R lr;                // length [cells] of the tissue-mechanism ramp in the layer
 };
 
-// Tissue mechanisms in the absorbing layer (two-stage layer, Sec. 4.4 /
+// Tissue mechanisms in the absorbing layer (two-stage layer, Sec. 4.6 /
 // Sec. 5.4): the strength of every tissue mechanism of a cell at depth s
 // into the layer (cells, largest over the axes, at the cell centre) is
 // r = 1 - (s/L_r)^2 for s < L_r, 0 beyond, at a fixed relaxation rate:
