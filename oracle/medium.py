@@ -144,10 +144,14 @@ class OracleMedium:
     dscale     : optional per-voxel factor s on every d of the tissue mechanisms
                  (d^nu(x) = s(x) d^nu_class), a map like alpha0 and inherited
                  into the absorbing layer like the other maps
+    layer_relax : keep the caller's class map inside the absorbing layer
+                 instead of inheriting it (the homogeneous layers compared
+                 with the adaptive one in Sec. 4.6: one fixed class there);
+                 c, rho and beta are inherited either way
     """
 
     def __init__(self, shape, dx, dt, c, rho, cls, params, beta=None, pml=0, transition=0,
-                 f0=3e6, R0=1e-5, periodic=None, dscale=None, tissue_ramp_on=True):
+                 f0=3e6, R0=1e-5, periodic=None, dscale=None, tissue_ramp_on=True, layer_relax=False):
         self.shape = tuple(shape)
         self.ndim = len(shape)
         self.dx, self.dt = float(dx), float(dt)
@@ -160,7 +164,7 @@ class OracleMedium:
         inh = lambda a, dt_: _inherit(np.asarray(a, dt_), width, self.abs_axes)  # noqa: E731
         c = inh(c, np.float64)
         rho = inh(rho, np.float64)
-        cls = inh(cls, np.int64)
+        cls = np.array(cls, np.int64) if layer_relax else inh(cls, np.int64)
         beta = None if beta is None else inh(beta, np.float64)
         self.c, self.rho, self.cls = c, rho, cls
         self.dscale = None if dscale is None else inh(dscale, np.float64)

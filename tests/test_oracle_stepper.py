@@ -29,13 +29,13 @@ def modified_wavenumber(k, dx):
 
 
 def sim_of(shape, dx, dt, c=1540.0, rho=1000.0, params=None, periodic=None, pml=0, transition=0,
-           beta=None, f0=1e6, cls=None):
+           beta=None, f0=1e6, cls=None, layer_relax=False):
     params = params or [fit.RelaxParams.lossless(2)]
     cmap = np.broadcast_to(np.asarray(c, float), shape)
     rmap = np.broadcast_to(np.asarray(rho, float), shape)
     cls = np.zeros(shape, np.int64) if cls is None else cls
     med = OracleMedium(shape, dx, dt, cmap, rmap, cls, params, beta=beta, pml=pml,
-                       transition=transition, f0=f0, periodic=periodic)
+                       transition=transition, f0=f0, periodic=periodic, layer_relax=layer_relax)
     return OracleSim(med)
 
 
@@ -322,8 +322,9 @@ def test_point_source_matches_2d_green_function(oracle_lib):
 
 
 def _plane_run(params, f0, depth_cells, rcv_rows, nt, ppw=16, cfl=0.2, pml=20, transition=0,
-               c=1540.0, rho=1000.0, beta=None, amp=1e3, tau=None, cls=None, layer_params=None):
-    """1D-like plane wave: 4 periodic columns, source row pml+transition+2."""
+               c=1540.0, rho=1000.0, beta=None, amp=1e3, tau=None, cls=None, layer_class=None):
+    """1D-like plane wave: 4 periodic columns, source row pml+transition+2.
+    layer_class: one fixed class in the whole absorbing layer (layer_relax)."""
     dx = c / (f0 * ppw)
     dt = cfl * dx / c
     width = pml + transition
@@ -331,8 +332,13 @@ def _plane_run(params, f0, depth_cells, rcv_rows, nt, ppw=16, cfl=0.2, pml=20, t
     shape = (ny, 4)
     if cls is None:
         cls = np.zeros(shape, np.int64)
+    if layer_class is not None:
+        cls = cls.copy()
+        cls[:width] = layer_class
+        cls[ny - width:] = layer_class
     sim = sim_of(shape, dx, dt, c, rho, params=params, periodic=(False, True), pml=pml,
-                 transition=transition, beta=None if beta is None else np.full(shape, beta), f0=f0, cls=cls)
+                 transition=transition, beta=None if beta is None else np.full(shape, beta), f0=f0, cls=cls,
+                 layer_relax=layer_class is not None)
     row = width + 2
     src = np.zeros(shape, np.uint8)
     src[row] = 1
@@ -360,6 +366,31 @@ def test_pml_reflection_below_minus_50db(a0, y, oracle_lib):
     big, _, _ = _plane_run([prm], f0, D + 600, rows, nt, ppw=ppw, pml=L, transition=L)
     R = measure.reflection_db(small.traces[0], big.traces[0])
     assert R < -50.0, R
+
+
+def test_homogeneous_layer_reflects_away_from_its_design_point(oracle_lib):
+    """Homogeneous layers (Sec. 4.6): one relaxation class, fitted for
+    (0.5, 1.0), in the whole layer instead of the inherited interior class.
+    At its own (alpha0, y) the medium is the adaptive one, so R is equal; for
+    an interior tissue away from it the relaxation set changes abruptly at the
+    layer's inner edge and R rises well above the adaptive layer's (Sec. 5.5:
+    the homogeneous layers degrade away from the design point)."""
+    ref, _ = fit.fit_relaxation(0.5, 1.0, 2, maxiter=1500, w_list=(0.5,))
+    f0, ppw = 1e6, 16
+    L = 3 * ppw
+    D = 5 * ppw
+    rows = [D - 8]
+    nt = 2000
+    out = {}
+    for a0, y in ((0.5, 1.0), (0.3, 0.7)):
+        prm, _ = fit.fit_relaxation(a0, y, 2, maxiter=1500, w_list=(0.5,))
+        for lc in (None, 1):
+            small, _, _ = _plane_run([prm, ref], f0, D, rows, nt, ppw=ppw, pml=L, transition=L, layer_class=lc)
+            big, _, _ = _plane_run([prm, ref], f0, D + 600, rows, nt, ppw=ppw, pml=L, transition=L, layer_class=lc)
+            out[(a0, y, lc)] = measure.reflection_db(small.traces[0], big.traces[0])
+    assert abs(out[(0.5, 1.0, None)] - out[(0.5, 1.0, 1)]) < 1e-6, out
+    assert out[(0.3, 0.7, None)] < -60.0, out
+    assert out[(0.3, 0.7, 1)] > out[(0.3, 0.7, None)] + 10.0, out
 
 
 def test_simulated_attenuation_and_dispersion(oracle_lib):
