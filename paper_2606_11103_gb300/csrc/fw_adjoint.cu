@@ -136,7 +136,7 @@ __global__ void k_adj_pres(const AdjArgs<R> A)
         const R lst = -A.kdt[i] * lp;
         // tissue ramp of the absorbing layer: a -> r a (the forward sweep's ce, r div)
         const R r = cell_ramp(A, P);
-        const R ce = t[3] + (r - R(1)) * (t[3] - fw_rcp(t[1]));   // the forward sweep's ceff
+        const R ce = t[3] + (r - R(1)) * t[kLutDk + 1];   // the forward sweep's ceff
         R stp = div * ce;
         R ldiv = ce * lst;
         double gs = 0.0;
@@ -181,7 +181,7 @@ __global__ void k_adj_vel(const AdjArgs<R> A)
         const R *dtb = A.dlut + (size_t)A.cls[i] * kDStride;
         const R own = A.rho[i];
         const R r = cell_ramp(A, P);
-        const R ce = t[2] + (r - R(1)) * (t[2] - fw_rcp(t[0]));
+        const R ce = t[2] + (r - R(1)) * t[kLutDk];
         double gs = 0.0;
         for (int ax = 0; ax < 3; ++ax) {
             if (!A.ax_on[ax]) continue;

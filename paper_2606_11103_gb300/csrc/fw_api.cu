@@ -310,14 +310,14 @@ std::vector<double> build_lut(const std::vector<fw_relax_params> &cl, double dt,
         double *e = &t[c * kLutStride];
         e[0] = p.kappa1;
         e[1] = p.kappa2;
-        double ce1 = 1.0 / p.kappa1, ce2 = 1.0 / p.kappa2;
+        double sa1 = 0.0, sa2 = 0.0;   // sum a/2 per stretch
         for (int m = 0; m < p.n_mech; ++m) {
             double b1 = std::exp(-(p.d1[m] / p.kappa1 + p.alpha1[m]) * dt);
             double a1 = p.d1[m] / (p.kappa1 * (p.d1[m] + p.kappa1 * p.alpha1[m])) * (b1 - 1.0);
             double b2 = std::exp(-(p.d2[m] / p.kappa2 + p.alpha2[m]) * dt);
             double a2 = p.d2[m] / (p.kappa2 * (p.d2[m] + p.kappa2 * p.alpha2[m])) * (b2 - 1.0);
-            ce1 += 0.5 * a1;
-            ce2 += 0.5 * a2;
+            sa1 += 0.5 * a1;
+            sa2 += 0.5 * a2;
             e[kLutA1 + m] = a1 * sc1;
             e[kLutB1 + m] = b1;
             e[kLutH1 + m] = 0.5 * (1.0 + b1) / sc1;
@@ -325,8 +325,10 @@ std::vector<double> build_lut(const std::vector<fw_relax_params> &cl, double dt,
             e[kLutB2 + m] = b2;
             e[kLutH2 + m] = 0.5 * (1.0 + b2) / sc2;
         }
-        e[2] = ce1;
-        e[3] = ce2;
+        e[2] = 1.0 / p.kappa1 + sa1;
+        e[3] = 1.0 / p.kappa2 + sa2;
+        e[kLutDk] = sa1;
+        e[kLutDk + 1] = sa2;
     }
     return t;
 }

@@ -31,8 +31,9 @@ int nelder_mead(int n, double *x, const double *lo, const double *hi,
 // ---- device layout ---------------------------------------------------------
 constexpr int kLutStride = 32;   // values per class in the coefficient table
 // table block offsets (in values): 0 kappa1, 1 kappa2, 2 ceff1, 3 ceff2,
-// 4.. a1[4], 8.. b1[4], 12.. hb1[4], 16.. a2[4], 20.. b2[4], 24.. hb2[4]
-constexpr int kLutA1 = 4, kLutB1 = 8, kLutH1 = 12, kLutA2 = 16, kLutB2 = 20, kLutH2 = 24;
+// 4.. a1[4], 8.. b1[4], 12.. hb1[4], 16.. a2[4], 20.. b2[4], 24.. hb2[4],
+// 28 sum a1/2, 29 sum a2/2 (= ceff - 1/kappa, the part the layer ramp scales)
+constexpr int kLutA1 = 4, kLutB1 = 8, kLutH1 = 12, kLutA2 = 16, kLutB2 = 20, kLutH2 = 24, kLutDk = 28;
 
 struct Monitor {
     unsigned int max_bits;   // bits of max |p| (non-negative float)

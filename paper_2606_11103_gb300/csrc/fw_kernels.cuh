@@ -240,11 +240,10 @@ __device__ __forceinline__ R layer_depth(int c, int n, int w)
 }
 
 template <typename R>
-__device__ __forceinline__ R ramp_of(R s, R inv_lr)
+__device__ __forceinline__ R ramp_of(R s, R inv_lr)   // s >= 0; exactly 1 at s = 0
 {
-    if (s <= R(0)) return R(1);
-    const R q = s * inv_lr;
-    return q < R(1) ? R(1) - q * q : R(0);
+    const R q = fmin(s * inv_lr, R(1));
+    return R(1) - q * q;
 }
 
 template <typename R, typename SS, typename SP> struct VelArgs {
@@ -434,7 +433,7 @@ k_velocity(const VelArgs<R, SS, SP> A)
         for (int e = 0; e < 4; ++e) sxy[e] = fmax(layer_depth<R>(x0 + e, G.nx, G.wabs), layer_depth<R>(y, G.ny, G.wabs));
     // class coefficients of the last class seen (classes rarely change along a column)
     int ccls = -1;
-    R hdr[4], A1[4], B1[4], H1[4], dk1 = R(0);   // dk1 = ceff1 - 1/kappa1 of the cached class
+    R hdr[4], A1[4], B1[4], H1[4], dk1 = R(0);   // dk1 = ceff1 - 1/kappa1 (sum a1/2) of the cached class
 
     for (int k = z0; k < z1; ++k) {
         const long long pk = (long long)k * G.plane;
@@ -532,7 +531,7 @@ k_velocity(const VelArgs<R, SS, SP> A)
                         lut4(A.lut, c, kLutA1, A1);
                         lut4(A.lut, c, kLutB1, B1);
                         lut4(A.lut, c, kLutH1, H1);
-                        dk1 = hdr[2] - fw_rcp(hdr[0]);
+                        dk1 = __ldg(A.lut + (size_t)c * kLutStride + kLutDk);
                         ccls = c;
                     }
                     // a dead lane (x >= nx) gets drive 0, so its memory variables stay exactly 0
@@ -673,7 +672,7 @@ k_pressure(const PresArgs<R, SS, SP> A)
 #pragma unroll
         for (int e = 0; e < 4; ++e) sxy[e] = fmax(layer_depth<R>(x0 + e, G.nx, G.wabs), layer_depth<R>(y, G.ny, G.wabs));
     int ccls = -1;
-    R hdr[4], A2[4], B2[4], H2[4], dk2 = R(0);   // dk2 = ceff2 - 1/kappa2 of the cached class
+    R hdr[4], A2[4], B2[4], H2[4], dk2 = R(0);   // dk2 = ceff2 - 1/kappa2 (sum a2/2) of the cached class
     for (int k = z0; k < z1; ++k) {
         const long long pk = (long long)k * G.plane;
         const int buf = k & 1;
@@ -746,7 +745,7 @@ k_pressure(const PresArgs<R, SS, SP> A)
                     lut4(A.lut, c, kLutA2, A2);
                     lut4(A.lut, c, kLutB2, B2);
                     lut4(A.lut, c, kLutH2, H2);
-                    dk2 = hdr[3] - fw_rcp(hdr[1]);
+                    dk2 = __ldg(A.lut + (size_t)c * kLutStride + kLutDk + 1);
                     ccls = c;
                 }
                 const bool live = x0 + e < G.nx;

@@ -87,3 +87,22 @@ class Pair:
         if self.orc.traces is not None and self.orc.traces.size:
             out["traces"] = rel_l2(self.gpu.receivers(f64=f64), self.orc.traces)
         return out
+
+
+_SETS = None
+
+
+def stored_set(alpha0, y):
+    """(RelaxParams, report) of the oracle fit at the paper's settings for
+    (alpha0, y), from tests/golden/relax_sets.json (written by
+    tests/golden/fit_relax_sets.py, which calls only the oracle)."""
+    global _SETS
+    if _SETS is None:
+        import json
+        import os
+        with open(os.path.join(os.path.dirname(__file__), "golden", "relax_sets.json")) as f:
+            _SETS = json.load(f)
+    d = _SETS["sets"]["%g,%g" % (alpha0, y)]
+    p = fit.RelaxParams(d["kappa1"], d["kappa2"], np.array(d["d1"]), np.array(d["alpha1"]), np.array(d["d2"]),
+                        np.array(d["alpha2"]))
+    return p, d
