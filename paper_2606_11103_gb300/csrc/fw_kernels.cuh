@@ -388,8 +388,10 @@ __device__ __forceinline__ void vel_issue(const VelArgs<R, SS, SP> &A, unsigned 
     }
 }
 
+// 3D: 32-bit memory variables fill shared memory at two CTAs per SM, 16-bit
+// ones fit three (registers are held to the matching share)
 template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY>
-__global__ void __launch_bounds__(BX *BY, DIM == 3 ? (BY < 8 ? 3 : 2) : 1)
+__global__ void __launch_bounds__(BX *BY, DIM == 3 ? ((BY < 8 && sizeof(SP) == 2) ? 3 : 2) : 1)
 k_velocity(const VelArgs<R, SS, SP> A)
 {
     using L = VelSmem<R, SS, SP, DIM, NM, BX, BY>;
@@ -434,6 +436,10 @@ k_velocity(const VelArgs<R, SS, SP> A)
     // class coefficients of the last class seen (classes rarely change along a column)
     int ccls = -1;
     R hdr[4], A1[4], B1[4], H1[4], dk1 = R(0);   // dk1 = ceff1 - 1/kappa1 (sum a1/2) of the cached class
+    // absorbing-mechanism coefficients along x and y of the four cells: fixed
+    // positions, so they change only with the cells' classes (their kappa)
+    R pxa[4], pxb[4], pya[4], pyb[4];
+    uint2 pkey = make_uint2(0xffffffffu, 0xffffffffu);
 
     for (int k = z0; k < z1; ++k) {
         const long long pk = (long long)k * G.plane;
@@ -511,6 +517,15 @@ k_velocity(const VelArgs<R, SS, SP> A)
 #pragma unroll
                 for (int e = 0; e < 4; ++e) rr[e] = ramp_of(fmax(sxy[e], sz), inv_lr);
             }
+            if ((pml_x || pml_y) && (cl.x != pkey.x || cl.y != pkey.y)) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const R kap = __ldg(A.lut + (size_t)cls4[e] * kLutStride);   // kappa1
+                    if (pml_x) pml_ab(pdx[e], pax[e], kap, G.dt, pxa[e], pxb[e]);
+                    if (pml_y) pml_ab(pdy, pay, kap, G.dt, pya[e], pyb[e]);
+                }
+                pkey = cl;
+            }
             // one direction at a time: its v and psi come from the stage
 #pragma unroll
             for (int ax = 0; ax < 3; ++ax) {
@@ -551,7 +566,9 @@ k_velocity(const VelArgs<R, SS, SP> A)
                         const R d = ax == 0 ? pdx[e] : (ax == 1 ? pdy : pdz);
                         if (d > R(0) && live) {
                             R a, b;
-                            pml_ab(d, ax == 0 ? pax[e] : (ax == 1 ? pay : paz), hdr[0], G.dt, a, b);
+                            if (ax == 0) { a = pxa[e]; b = pxb[e]; }
+                            else if (ax == 1) { a = pya[e]; b = pyb[e]; }
+                            else pml_ab(d, paz, hdr[0], G.dt, a, b);
                             const R po = pp[e];
                             stv += R(0.5) * (R(1) + b) * po + R(0.5) * a * gd;
                             pp[e] = b * po + a * gd;
