@@ -690,6 +690,9 @@ k_pressure(const PresArgs<R, SS, SP> A)
         for (int e = 0; e < 4; ++e) sxy[e] = fmax(layer_depth<R>(x0 + e, G.nx, G.wabs), layer_depth<R>(y, G.ny, G.wabs));
     int ccls = -1;
     R hdr[4], A2[4], B2[4], H2[4], dk2 = R(0);   // dk2 = ceff2 - 1/kappa2 (sum a2/2) of the cached class
+    // absorbing-mechanism coefficients along x and y, recomputed only when the cells' classes change
+    R pxa[4], pxb[4], pya[4], pyb[4];
+    uint2 pkey = make_uint2(0xffffffffu, 0xffffffffu);
     for (int k = z0; k < z1; ++k) {
         const long long pk = (long long)k * G.plane;
         const int buf = k & 1;
@@ -754,6 +757,15 @@ k_pressure(const PresArgs<R, SS, SP> A)
 #pragma unroll
                 for (int e = 0; e < 4; ++e) rr[e] = ramp_of(fmax(sxy[e], sz), inv_lr);
             }
+            if ((pml_x || pml_y) && (cl.x != pkey.x || cl.y != pkey.y)) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const R kap = __ldg(A.lut + (size_t)cls4[e] * kLutStride + 1);   // kappa2
+                    if (pml_x) pml_ab(pdx[e], pax[e], kap, G.dt, pxa[e], pxb[e]);
+                    if (pml_y) pml_ab(pdy, pay, kap, G.dt, pya[e], pyb[e]);
+                }
+                pkey = cl;
+            }
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int c = cls4[e];
@@ -786,7 +798,9 @@ k_pressure(const PresArgs<R, SS, SP> A)
                     const R d = ax == 0 ? pdx[e] : (ax == 1 ? pdy : pdz);
                     if (d > R(0) && live) {
                         R a, b;
-                        pml_ab(d, ax == 0 ? pax[e] : (ax == 1 ? pay : paz), hdr[1], G.dt, a, b);
+                        if (ax == 0) { a = pxa[e]; b = pxb[e]; }
+                        else if (ax == 1) { a = pya[e]; b = pyb[e]; }
+                        else pml_ab(d, paz, hdr[1], G.dt, a, b);
                         const R po = pp[ax][e];
                         stp += R(0.5) * (R(1) + b) * po + R(0.5) * a * qd[ax][e];
                         pp[ax][e] = b * po + a * qd[ax][e];
