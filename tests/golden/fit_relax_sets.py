@@ -9,6 +9,9 @@ the (alpha0, y) pairs the validation experiments use:
 * the tissues of the two-layer models of Sec. 4.4 / Table 4: muscle
   (0.15, 1.0), fat (0.40, 1.1), liver (0.50, 1.1).
 
+Each pair also keeps the set fitted at every weight (per_w), the
+candidates of the simulation-based weight selection of Sec. 3.2.
+
 Only the oracle is called.  Run from the repository root:
     python tests/golden/fit_relax_sets.py
 """
@@ -29,13 +32,20 @@ def key(a0, y):
     return "%g,%g" % (a0, y)
 
 
+def _params(p):
+    fl = lambda v: [float(x) for x in v]  # noqa: E731
+    return dict(kappa1=float(p.kappa1), kappa2=float(p.kappa2), d1=fl(p.d1), alpha1=fl(p.alpha1), d2=fl(p.d2),
+                alpha2=fl(p.alpha2))
+
+
 def _one(pair):
     from oracle import fit
     p, rep = fit.fit_relaxation(pair[0], pair[1], 2)
-    fl = lambda v: [float(x) for x in v]  # noqa: E731
-    return pair, dict(kappa1=float(p.kappa1), kappa2=float(p.kappa2), d1=fl(p.d1), alpha1=fl(p.alpha1),
-                      d2=fl(p.d2), alpha2=fl(p.alpha2), nrmse=float(rep.nrmse), disp_rmse=float(rep.disp_rmse),
-                      w=float(rep.w), failed=bool(rep.failed))
+    d = _params(p)
+    d.update(nrmse=float(rep.nrmse), disp_rmse=float(rep.disp_rmse), w=float(rep.w), failed=bool(rep.failed))
+    d["per_w"] = [dict(_params(e["params"]), w=float(e["w"]), nrmse=float(e["nrmse"]), disp_rmse=float(e["disp"]))
+                  for e in rep.per_w]
+    return pair, d
 
 
 def main():

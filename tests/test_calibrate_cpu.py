@@ -1,0 +1,47 @@
+"""Host side of the simulation-based weight selection (calibrate.py), no
+GPU: the spectral measurement recovers a prescribed attenuation and phase
+velocity exactly, and the power-law and Kramers-Kronig targets agree with
+the oracle's own implementation of Eqs. power_law_attenuation and
+kk_relation."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import fit
+
+cal = pytest.importorskip("paper_2606_11103_gb300.calibrate")
+
+
+@pytest.mark.parametrize("a0,y", [(0.5, 1.0), (0.75, 1.5), (0.25, 0.6)])
+def test_targets_match_the_oracle(a0, y):
+    f = np.linspace(1e6, 20e6, 37)
+    assert np.allclose(cal.alpha_target(a0, y, f), fit.alpha_target(a0, y, f), rtol=1e-12, atol=0)
+    c_or = 1.0 / fit.inv_c_target(a0, y, 2 * math.pi * f, 1540.0)
+    assert np.allclose(cal.phase_velocity_target(a0, y, f, 1540.0), c_or, rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("f0", [1e6, 9.13e6, 19.97e6])
+def test_spectral_measurement_recovers_a_prescribed_medium(f0):
+    """Trace 2 = trace 1 filtered by exp(-alpha(f) d - i w d / c(f)) with a
+    power-law alpha and the Kramers-Kronig c: the measured alpha and c
+    equal the prescribed ones over the band."""
+    a0, y, c0 = 0.6, 1.3, 1540.0
+    ppw, cfl = 16, 0.2
+    dx = c0 / (f0 * ppw)
+    dt = cfl * dx / c0
+    d = 120 * dx
+    n = 4096
+    tr1 = cal.gaussian_pulse(f0, dt, n)
+    N = 1 << 16
+    f = np.fft.rfftfreq(N, dt)
+    fm = np.maximum(f, 1.0)
+    H = np.exp(-cal.alpha_target(a0, y, fm) * d - 1j * 2 * math.pi * fm * d / cal.phase_velocity_target(a0, y, fm, c0))
+    tr2 = np.fft.irfft(np.fft.rfft(tr1, N) * H, N)[:n]
+    fb, ratio, phi = cal.spectra_between(tr1, tr2, dt, f0)
+    assert fb.size > 10 and fb.min() >= 0.7 * f0 and fb.max() <= 1.3 * f0
+    w = 2 * math.pi * fb
+    k = np.round((w[len(w) // 2] * d / c0 - phi[len(phi) // 2]) / (2 * math.pi))
+    c = w * d / (phi + 2 * math.pi * k)
+    assert np.allclose(-np.log(ratio) / d, cal.alpha_target(a0, y, fb), rtol=1e-6, atol=0)
+    assert np.allclose(c, cal.phase_velocity_target(a0, y, fb, c0), rtol=1e-9, atol=0)
