@@ -267,11 +267,17 @@ def time_oracle(budget_s, crop=128):
                       "%.1f s" % (crop, k, dt)}
 
 
+def workload_config(args, l2, parallelism):
+    """The config object both arms print (the reference arm times a crop of it)."""
+    return {"workload": "3D seeded Voronoi %d^3, 8 classes, N=4, 20-cell PML, focused 3 MHz aperture" % args.size,
+            "voxels": args.size ** 3, "storage": args.storage, "l2": l2, "parallelism": parallelism}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    crop = 96
+    crop = 128
     sim, vox = oracle_sim(crop, n_steps=args.warmup + args.steps + 1)
     sim.run(args.warmup)
     t0 = time.perf_counter()
@@ -282,9 +288,11 @@ def run_reference(args):
     out = {"impl": "reference", "metric": "voxel-updates/s (3D FP32)", "value": v, "unit": "Gvoxel-updates/s",
            "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": "3D Voronoi 512^3 N=4, FP64 CPU oracle on a %d^3 crop" % crop},
+           "data": "synthetic",
+           "config": workload_config(args, "host cores (FP64 CPU oracle)", "host threads"),
            "cpu_baseline": {"value": v, "unit": "Gvoxel-updates/s", "cores": cores, "kind": "oracle",
-                            "sample": "%d^3 crop, %d steps" % (crop, args.steps)},
+                            "sample": "FP64 C oracle on a %d^3 crop of the workload, %d timed steps after %d"
+                                      % (crop, args.steps, args.warmup)},
            "e2e": {"value": v, "unit": "Gvoxel-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -403,10 +411,8 @@ def run_ours(args):
         "n_gpus": ws, "steps": K, "warmup": W, "ms_per_step": round(ms / K, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.storage == "f32" else "f32/%s-psi" % args.storage,
         "data": "synthetic",
-        "config": {"workload": "3D seeded Voronoi %d^3, 8 classes, N=4, 20-cell PML, focused 3 MHz aperture"
-                               % args.size, "voxels": vox, "storage": args.storage,
-                   "l2": "working set %.1f GB >> 129 MB L2, no flush needed" % (info["device_bytes"] / 1e9),
-                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "config": workload_config(args, "working set %.1f GB >> 129 MB L2, no flush needed" % (info["device_bytes"] / 1e9),
+                                  "replicas" if ws > 1 else "single GPU"),
         "e2e": {"value": round(e2e, 3), "unit": "Gvoxel-updates/s", "h2d_bytes_per_step": nw * 4,
                 "d2h_bytes_per_step": nr * 4, "steps": K2},
         "gpu_launches": int(nl.value),
