@@ -261,7 +261,8 @@ def time_oracle(budget_s, crop=128):
     t0 = time.perf_counter()
     sim.run(k)
     dt = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    from oracle import stepper
+    cores = stepper.threads()
     return {"value": vox * k / dt / 1e9, "unit": "Gvoxel-updates/s", "cores": cores, "kind": "oracle",
             "sample": "FP64 C oracle, %d^3 crop of the 512^3 Voronoi workload (N=4, 20-cell PML), %d time steps, "
                       "%.1f s" % (crop, k, dt)}
@@ -284,7 +285,8 @@ def run_reference(args):
     sim.run(args.steps)
     dt = time.perf_counter() - t0
     v = vox * args.steps / dt / 1e9
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    from oracle import stepper
+    cores = stepper.threads()
     out = {"impl": "reference", "metric": "voxel-updates/s (3D FP32)", "value": v, "unit": "Gvoxel-updates/s",
            "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",

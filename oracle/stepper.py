@@ -62,7 +62,13 @@ def lib():
                                  C.c_int, C.POINTER(C.c_long), _P, C.c_int, C.c_int]
         _lib.orc_dplus.argtypes = [C.POINTER(_Coeffs), _P, _P, C.c_int]
         _lib.orc_dminus.argtypes = [C.POINTER(_Coeffs), _P, _P, C.c_int]
+        _lib.orc_threads.restype = C.c_int
     return _lib
+
+
+def threads():
+    """Host threads the C stepper runs on."""
+    return int(lib().orc_threads())
 
 
 def _ptr(a):
