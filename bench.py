@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=0, help="streaming end-to-end steps (0: = --steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", default="voronoi3d", choices=["voronoi3d", "serving"],
+    ap.add_argument("--workload", default="voronoi3d", choices=["voronoi3d", "twolayer2d", "serving"],
                     help="serving: the mixed 2D/3D request stream through the continuous-batching server")
     ap.add_argument("--requests", type=int, default=40, help="serving: requests in the stream (200 = full mix)")
     ap.add_argument("--slots", type=int, default=8, help="serving: admitted requests at once")
@@ -95,7 +95,16 @@ def allmax(x, ws):
 
 
 def workload(args, n_steps):
-    from synthetic import config_c3
+    """The synthetic workload: the 3D Voronoi medium (default) or the 2D
+    two-layer nonlinear medium; returns (spec, class map, class list for the
+    calibration as (alpha0, y, c) triples, beta map or None)."""
+    from synthetic import config_c2, config_c3
+    if args.workload == "twolayer2d":
+        spec = config_c2(n_steps=n_steps)
+        la, lb = spec.extra["layer_a"], spec.extra["layer_b"]
+        n = spec.shape[0]
+        cls = ((np.arange(n)[:, None] >= spec.extra["interface"]) * np.ones(spec.shape)).astype(np.uint16)
+        return spec, cls, [(la["alpha0"], la["y"], la["c"]), (lb["alpha0"], lb["y"], lb["c"])], spec.maps["beta"]
     n = args.size
     if n == 512:
         spec = config_c3(n_steps=n_steps)
@@ -103,18 +112,19 @@ def workload(args, n_steps):
         lo = (512 - n) // 2
         box = ((0, n), (lo, lo + n), (lo, lo + n))
         spec = config_c3(n_steps=n_steps, box=box)
-    return spec
+    triples = list(zip(spec.classes["alpha0"], spec.classes["y"], spec.classes["c"]))
+    return spec, spec.maps["class_idx"], triples, None
 
 
-def fit_classes(spec):
-    """Host FP64 calibration of every class (paper settings), one thread per class."""
+def fit_classes(triples):
+    """Host FP64 calibration of every (alpha0, y, c) class (paper settings), one thread per class."""
     import paper_2606_11103_gb300 as fw
-    out = [None] * len(spec.classes["alpha0"])
+    out = [None] * len(triples)
     reps = [None] * len(out)
 
     def job(i):
-        out[i], reps[i] = fw.fit_relaxation(float(spec.classes["alpha0"][i]), float(spec.classes["y"][i]), 4,
-                                            c0=float(spec.classes["c"][i]))
+        a, y, c = triples[i]
+        out[i], reps[i] = fw.fit_relaxation(float(a), float(y), 4, c0=float(c))
 
     th = [threading.Thread(target=job, args=(i,)) for i in range(len(out))]
     for t in th:
@@ -232,27 +242,48 @@ class ClockSampler:
 # oracle timing (cpu_baseline leg and the reference arm)
 
 
-def oracle_sim(crop=128, n_steps=8):
+ORACLE_CROP = {"voronoi3d": 128, "twolayer2d": 768}
+
+
+def oracle_sample(kind):
+    crop = ORACLE_CROP[kind]
+    if kind == "twolayer2d":
+        return "%d^2 two-layer medium of the same kind (N=4, nonlinear, 30-cell PML)" % crop
+    return "%d^3 crop of the 512^3 Voronoi workload (N=4, 20-cell PML)" % crop
+
+
+def oracle_sim(kind, n_steps=8):
     from oracle import fit
     from oracle.medium import OracleMedium
     from oracle.stepper import OracleSim
-    from synthetic import config_c3
-    lo = (512 - crop) // 2
-    spec = config_c3(n_steps=n_steps, box=((0, crop), (lo, lo + crop), (lo, lo + crop)))
+    from synthetic import config_c2, config_c3
+    crop = ORACLE_CROP[kind]
+    if kind == "twolayer2d":
+        spec = config_c2(n=crop, n_steps=n_steps)
+        la, lb = spec.extra["layer_a"], spec.extra["layer_b"]
+        triples = [(la["alpha0"], la["y"]), (lb["alpha0"], lb["y"])]
+        cls = ((np.arange(crop)[:, None] >= spec.extra["interface"]) * np.ones(spec.shape)).astype(np.int64)
+        beta = spec.maps["beta"].astype(np.float64)
+    else:
+        lo = (512 - crop) // 2
+        spec = config_c3(n_steps=n_steps, box=((0, crop), (lo, lo + crop), (lo, lo + crop)))
+        triples = list(zip(spec.classes["alpha0"], spec.classes["y"]))
+        cls = spec.maps["class_idx"].astype(np.int64)
+        beta = None
     params = []
-    for a, y in zip(spec.classes["alpha0"], spec.classes["y"]):
+    for a, y in triples:
         p, _ = fit.fit_relaxation(float(a), float(y), 4, maxiter=200, w_list=(0.5,))
         params.append(p)
-    med = OracleMedium(spec.shape, spec.dx, spec.dt, spec.maps["c"], spec.maps["rho"],
-                       spec.maps["class_idx"].astype(np.int64), params, pml=spec.pml, f0=spec.f0)
+    med = OracleMedium(spec.shape, spec.dx, spec.dt, spec.maps["c"], spec.maps["rho"], cls, params, beta=beta,
+                       pml=spec.pml, f0=spec.f0)
     sim = OracleSim(med)
     sim.set_sources(spec.src_mask, spec.src_waves.astype(np.float64), spec.src_wave_of)
     sim.set_receivers(spec.rcv_mask, n_steps)
     return sim, int(np.prod(spec.shape))
 
 
-def time_oracle(budget_s, crop=128):
-    sim, vox = oracle_sim(crop, n_steps=4096)
+def time_oracle(budget_s, kind="voronoi3d"):
+    sim, vox = oracle_sim(kind, n_steps=4096)
     sim.run(1)                      # thread start-up
     t0 = time.perf_counter()
     sim.run(2)
@@ -264,12 +295,19 @@ def time_oracle(budget_s, crop=128):
     from oracle import stepper
     cores = stepper.threads()
     return {"value": vox * k / dt / 1e9, "unit": "Gvoxel-updates/s", "cores": cores, "kind": "oracle",
-            "sample": "FP64 C oracle, %d^3 crop of the 512^3 Voronoi workload (N=4, 20-cell PML), %d time steps, "
-                      "%.1f s" % (crop, k, dt)}
+            "sample": "FP64 C oracle, %s, %d time steps, %.1f s" % (oracle_sample(kind), k, dt)}
+
+
+def metric_name(args):
+    return "voxel-updates/s (2D FP32)" if args.workload == "twolayer2d" else "voxel-updates/s (3D FP32)"
 
 
 def workload_config(args, l2, parallelism):
     """The config object both arms print (the reference arm times a crop of it)."""
+    if args.workload == "twolayer2d":
+        return {"workload": "2D two-layer 2048^2 (c 1580/1450, rho 1060/950, alpha0 1.09/0.6, y 1.0/1.5, "
+                            "beta 3.5/6), N=4, 30-cell PML, 3 MHz line source",
+                "voxels": 2048 ** 2, "storage": args.storage, "l2": l2, "parallelism": parallelism}
     return {"workload": "3D seeded Voronoi %d^3, 8 classes, N=4, 20-cell PML, focused 3 MHz aperture" % args.size,
             "voxels": args.size ** 3, "storage": args.storage, "l2": l2, "parallelism": parallelism}
 
@@ -278,8 +316,7 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    crop = 128
-    sim, vox = oracle_sim(crop, n_steps=args.warmup + args.steps + 1)
+    sim, vox = oracle_sim(args.workload, n_steps=args.warmup + args.steps + 1)
     sim.run(args.warmup)
     t0 = time.perf_counter()
     sim.run(args.steps)
@@ -287,14 +324,14 @@ def run_reference(args):
     v = vox * args.steps / dt / 1e9
     from oracle import stepper
     cores = stepper.threads()
-    out = {"impl": "reference", "metric": "voxel-updates/s (3D FP32)", "value": v, "unit": "Gvoxel-updates/s",
+    out = {"impl": "reference", "metric": metric_name(args), "value": v, "unit": "Gvoxel-updates/s",
            "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",
            "config": workload_config(args, "host cores (FP64 CPU oracle)", "host threads"),
            "cpu_baseline": {"value": v, "unit": "Gvoxel-updates/s", "cores": cores, "kind": "oracle",
-                            "sample": "FP64 C oracle on a %d^3 crop of the workload, %d timed steps after %d"
-                                      % (crop, args.steps, args.warmup)},
+                            "sample": "FP64 C oracle on a %s, %d timed steps after %d"
+                                      % (oracle_sample(args.workload), args.steps, args.warmup)},
            "e2e": {"value": v, "unit": "Gvoxel-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -322,17 +359,17 @@ def run_ours(args):
     K2 = args.e2e_steps or K
     n_total = W + K + K2 + 2
     t0 = time.perf_counter()
-    spec = workload(args, n_total)
+    spec, cls_map, triples, beta = workload(args, n_total)
     t_gen = time.perf_counter() - t0
     t0 = time.perf_counter()
-    classes, reps = fit_classes(spec)
+    classes, reps = fit_classes(triples)
     t_fit = time.perf_counter() - t0
     log("workload %s generated in %.1fs, %d classes fitted in %.1fs (max NRMSE %.3f)" %
         (spec.name, t_gen, len(classes), t_fit, max(r.nrmse for r in reps)))
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
-    m = fw.Medium.from_classes(spec.shape, spec.dx, spec.maps["c"], spec.maps["rho"], spec.maps["class_idx"],
-                               classes, dt=spec.dt, pml=spec.pml, f0=spec.f0, storage=args.storage)
+    m = fw.Medium.from_classes(spec.shape, spec.dx, spec.maps["c"], spec.maps["rho"], cls_map, classes,
+                               dt=spec.dt, beta=beta, pml=spec.pml, f0=spec.f0, storage=args.storage)
     m.set_sources(spec.src_mask, spec.src_waves, spec.src_wave_of)
     m.set_receivers(spec.rcv_mask, n_total)
     t_create = time.perf_counter() - t0
@@ -389,12 +426,13 @@ def run_ours(args):
     assert np.isfinite(h_r.numpy()).all()
 
     # ---- roofline of the dominant kernel (velocity sweep) ----
-    b_vel, b_pres, b_single = alg_bytes(3, 4, args.storage, False, spec.pml, spec.shape)
+    b_vel, b_pres, b_single = alg_bytes(len(spec.shape), 4, args.storage, beta is not None, spec.pml, spec.shape)
     peak, peak_kind = measured_peaks()
     t_vel = ms_v.value / K / 1e3
     t_pres = ms_p.value / K / 1e3
     ach = b_vel * vox / t_vel / 1e9
-    traffic = profiled_traffic(vox, "velocity" if args.storage == "f32" else "velocity_" + args.storage)
+    tkey = "velocity" if args.storage == "f32" else "velocity_" + args.storage
+    traffic = profiled_traffic(vox, tkey + ("_2d" if args.workload == "twolayer2d" else ""))
     roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
             "frac": round(ach / peak, 4), "traffic": traffic, "kernel": "k_velocity (velocity sweep)",
             "peak_source": "%s hbm_gbs" % peak_kind}
@@ -409,7 +447,7 @@ def run_ours(args):
         "frac_step_vs_single_pass_min": round(b_single * vox * K / (ms / 1e3) / 1e9 / peak, 4),
     }
     out = {
-        "metric": "voxel-updates/s (3D FP32)", "value": round(value, 3), "unit": "Gvoxel-updates/s",
+        "metric": metric_name(args), "value": round(value, 3), "unit": "Gvoxel-updates/s",
         "n_gpus": ws, "steps": K, "warmup": W, "ms_per_step": round(ms / K, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.storage == "f32" else "f32/%s-psi" % args.storage,
         "data": "synthetic",
@@ -425,7 +463,7 @@ def run_ours(args):
     }
     m.close()
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = time_oracle(args.cpu_seconds)
+        out["cpu_baseline"] = time_oracle(args.cpu_seconds, args.workload)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
