@@ -48,9 +48,10 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=0, help="streaming end-to-end steps (0: = --steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", default="voronoi3d", choices=["voronoi3d", "twolayer2d", "serving"],
+    ap.add_argument("--workload", default="voronoi3d", choices=["voronoi3d", "twolayer2d", "serving", "adjoint"],
                     help="serving: the mixed 2D/3D request stream through the continuous-batching server")
     ap.add_argument("--requests", type=int, default=40, help="serving: requests in the stream (200 = full mix)")
+    ap.add_argument("--gradients", type=int, default=3, help="adjoint: timed gradients")
     ap.add_argument("--slots", type=int, default=8, help="serving: admitted requests at once")
     ap.add_argument("--load", type=float, default=0.8, help="serving: offered load / one-at-a-time capacity")
     return ap.parse_args()
@@ -596,12 +597,153 @@ def run_serving(args):
     print(json.dumps(out), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# adjoint workload: gradients of a receiver misfit (fw_gradient)
+
+
+def adjoint_alg_bytes(ndim, nmech, wabs, shape):
+    """Algorithmic bytes per voxel and time step of one gradient: the forward
+    run and the recomputation of each segment (two forward steps), the state
+    image of every recomputed step written and read back once, the adjoint
+    state read and written once, two FP64 gradient accumulators read and
+    written once, the material maps and class index read once."""
+    vel, pres, _ = alg_bytes(ndim, nmech, "f32", False, wabs, shape)
+    state = (1 + ndim + ndim * nmech + nmech) * 4
+    return 2 * (vel + pres) + 2 * state + 2 * state + 2 * 2 * 8 + (4 + 4 + 2)
+
+
+def oracle_gradient_rate(budget_s):
+    """FP64 oracle adjoint on a 192^2 crop of the adjoint workload (same
+    classes and protocol), voxel-steps per second of the whole gradient."""
+    from oracle import fit
+    from oracle.adjoint import misfit_gradient
+    from oracle import stepper
+    from synthetic import config_c5
+    n, steps = 192, 300
+    spec = config_c5(n=n, n_steps=steps)
+    params = [fit.fit_relaxation(float(a), float(y), 3, maxiter=200, w_list=(0.5,))[0]
+              for a, y in zip(spec.classes["alpha0"], spec.classes["y"])]
+    cls = spec.maps["class_idx"].astype(np.int64)
+    rng = np.random.default_rng(5)
+    G = rng.standard_normal((int(spec.rcv_mask.sum()), steps))
+    t0 = time.perf_counter()
+    misfit_gradient(spec.shape, spec.dx, spec.dt, spec.maps["c"].astype(np.float64),
+                    spec.maps["rho"].astype(np.float64), cls, params, np.asarray(spec.classes["alpha0"]), steps,
+                    spec.src_mask, spec.src_waves.astype(np.float64), spec.rcv_mask, G=G, pml=spec.pml, f0=spec.f0,
+                    checkpoint=30)
+    dt = time.perf_counter() - t0
+    return {"value": n * n * steps / dt / 1e9, "unit": "Gvoxel-steps/s", "cores": stepper.threads(),
+            "kind": "oracle", "sample": "FP64 oracle adjoint (Python driver, C stepper), %d^2 crop of the "
+                                        "adjoint workload, %d steps, checkpoint 30, %.1f s" % (n, steps, dt)}
+
+
+def run_adjoint(args):
+    """Gradient of a receiver functional on the 1024^2 Voronoi adjoint
+    workload (6 classes, N=3, 64 receivers, 3000 steps, checkpoint every
+    100): whole gradients (forward with checkpoints, recomputation, adjoint)
+    timed with device-resident G, alpha0 and outputs; e2e with host buffers."""
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    import paper_2606_11103_gb300 as fw
+    from paper_2606_11103_gb300 import build as fwbuild
+    from synthetic import config_c5
+    fwbuild.build()
+    spec = config_c5()
+    triples = list(zip(spec.classes["alpha0"], spec.classes["y"], spec.classes["c"]))
+    t0 = time.perf_counter()
+    out_cls = [None] * len(triples)
+
+    def job(i):
+        a, y, c = triples[i]
+        out_cls[i] = fw.fit_relaxation(float(a), float(y), 3, c0=float(c))[0]
+
+    th = [threading.Thread(target=job, args=(i,)) for i in range(len(triples))]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    log("adjoint workload: %d classes fitted in %.1fs" % (len(triples), time.perf_counter() - t0))
+    cls = spec.maps["class_idx"]
+    m = fw.Medium.from_classes(spec.shape, spec.dx, spec.maps["c"], spec.maps["rho"], cls, out_cls, dt=spec.dt,
+                               pml=spec.pml, f0=spec.f0)
+    m.set_sources(spec.src_mask, spec.src_waves)
+    n_steps = spec.n_steps
+    m.set_receivers(spec.rcv_mask, n_steps)
+    nr = int(m.info()["n_rcv"])
+    rng = np.random.default_rng(6)
+    G_h = rng.standard_normal((nr, n_steps)).astype(np.float32)
+    a0_h = np.asarray(spec.classes["alpha0"], np.float32)[cls]
+    dev = torch.device("cuda", local)
+    G_d, a0_d = torch.from_numpy(G_h).to(dev), torch.from_numpy(a0_h).to(dev)
+    out_d = (torch.empty(spec.shape, dtype=torch.float32, device=dev),
+             torch.empty(spec.shape, dtype=torch.float32, device=dev))
+    start = m.save_state(out=torch.empty(m.state_bytes(), dtype=torch.uint8, device=dev))
+    stream = torch.cuda.current_stream()
+    K, W = max(1, args.gradients), 1
+    for _ in range(W):
+        m.load_state(start)
+        m.gradient(n_steps, G_d, alpha0=a0_d, checkpoint=100, out=out_d)
+    torch.cuda.synchronize()
+    times = []
+    with ClockSampler(local) as clk:
+        for _ in range(K):
+            m.load_state(start)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            m.gradient(n_steps, G_d, alpha0=a0_d, checkpoint=100, out=out_d)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+    assert torch.isfinite(out_d[0]).all() and torch.isfinite(out_d[1]).all()
+    # end to end: G and alpha0 from host memory, gradients back to host memory
+    out_h = (np.empty(spec.shape, np.float32), np.empty(spec.shape, np.float32))
+    m.load_state(start)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    m.gradient(n_steps, G_h, alpha0=a0_h, checkpoint=100, out=out_h)
+    t_e2e = time.perf_counter() - t0
+    m.close()
+    vox = int(np.prod(spec.shape))
+    t = float(np.median(times))
+    value = vox * n_steps / t / 1e9
+    b = adjoint_alg_bytes(2, 3, spec.pml, spec.shape)
+    peak, peak_kind = measured_peaks()
+    ach = b * vox * n_steps / t / 1e9
+    out = {"metric": "gradient voxel-steps/s (2D FP32 adjoint)", "value": round(value, 3), "unit": "Gvoxel-steps/s",
+           "n_gpus": 1, "steps": K, "warmup": W, "ms_per_step": round(t * 1e3, 2), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "2D Voronoi 1024^2, 6 classes, N=3, 20-cell PML, 64 receivers, 3000 steps per "
+                                  "gradient, checkpoint every 100", "voxels": vox, "storage": "f32",
+                      "l2": "state images %.1f GB >> 129 MB L2" % ((n_steps // 100 + 103) * m_state_gb(spec)),
+                      "parallelism": "single GPU", "step": "one whole gradient"},
+           "e2e": {"value": round(vox * n_steps / t_e2e / 1e9, 3), "unit": "Gvoxel-steps/s",
+                   "h2d_bytes_per_step": G_h.nbytes + a0_h.nbytes, "d2h_bytes_per_step": 2 * out_h[0].nbytes},
+           "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                        "frac": round(ach / peak, 4), "traffic": None,
+                        "kernel": "fw_gradient as a whole (%.1f B per voxel-step)" % b,
+                        "peak_source": "%s hbm_gbs" % peak_kind},
+           "gradient_s": [round(x, 4) for x in times],
+           "clocks": clk.summary()}
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = oracle_gradient_rate(args.cpu_seconds)
+    print(json.dumps(out), flush=True)
+
+
+def m_state_gb(spec):
+    # p, v (2), psi1 (2 x 3), psi2 (3) and the absorbing-layer memory, FP32
+    return (1 + 2 + 6 + 3 + 4) * 4 * int(np.prod(spec.shape)) / 1e9
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.workload == "adjoint":
+        run_adjoint(args)
     else:
         run_ours(args)
 
