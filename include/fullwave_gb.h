@@ -320,7 +320,8 @@ int fw_load_state(fw_medium *m, const void *src, void *stream);
  * grad_alpha0 may be NULL.  Device memory: (ceil(n_steps/K) + K + 3) state
  * images (fw_state_bytes) plus 6 fields and 4 FP64 maps, from the installed
  * allocator, released before return.  Blocking.
- * Errors: FW_ERR_ARG, FW_ERR_UNSUPPORTED (nonlinear media, 16-bit storage),
+ * Errors: FW_ERR_ARG, FW_ERR_UNSUPPORTED (nonlinear media, 16-bit storage, more
+ * than 65535 points along either of the two slower axes),
  * FW_ERR_NOMEM, FW_ERR_CUDA, or the medium's sticky error. */
 int fw_gradient(fw_medium *m, int n_steps, int checkpoint_every, const void *G, const void *alpha0,
                 void *grad_c, void *grad_alpha0, int as_f64, void *stream);

@@ -75,17 +75,19 @@ template <typename R> struct Pt {
     long long st[3];   // strides
 };
 
+// One thread per point: x from the block's x range and thread, the other two
+// kernel axes from the grid's y and z (no division of a flat index).
 template <typename R>
-__device__ __forceinline__ bool decode(const AdjArgs<R> &A, long long i, Pt<R> &p)
+__device__ __forceinline__ bool point(const AdjArgs<R> &A, Pt<R> &p, long long &i)
 {
-    const int x = int(i % A.px);
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= A.nx) return false;
-    const long long r = i / A.px;
     p.c[0] = x;
-    p.c[1] = int(r % A.ny);
-    p.c[2] = int(r / A.ny);
+    p.c[1] = blockIdx.y;
+    p.c[2] = blockIdx.z;
     p.n[0] = A.nx; p.n[1] = A.ny; p.n[2] = A.nz;
     p.st[0] = 1; p.st[1] = A.px; p.st[2] = A.plane;
+    i = (long long)blockIdx.z * A.plane + (long long)blockIdx.y * A.px + x;
     return true;
 }
 
@@ -120,10 +122,10 @@ __device__ __forceinline__ R cell_ramp(const AdjArgs<R> &A, const Pt<R> &P)
 template <typename R>
 __global__ void k_adj_pres(const AdjArgs<R> A)
 {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < A.vol;
-         i += (long long)gridDim.x * blockDim.x) {
-        Pt<R> P;
-        if (!decode(A, i, P)) continue;
+    Pt<R> P;
+    long long i;
+    if (!point(A, P, i)) return;
+    {
         const R *t = A.lut + (size_t)A.cls[i] * kLutStride;
         const R *dtb = A.dlut + (size_t)A.cls[i] * kDStride;
         R q[3] = {0, 0, 0}, div = 0;
@@ -173,10 +175,10 @@ __global__ void k_adj_pres(const AdjArgs<R> A)
 template <typename R>
 __global__ void k_adj_vel(const AdjArgs<R> A)
 {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < A.vol;
-         i += (long long)gridDim.x * blockDim.x) {
-        Pt<R> P;
-        if (!decode(A, i, P)) continue;
+    Pt<R> P;
+    long long i;
+    if (!point(A, P, i)) return;
+    {
         const R *t = A.lut + (size_t)A.cls[i] * kLutStride;
         const R *dtb = A.dlut + (size_t)A.cls[i] * kDStride;
         const R own = A.rho[i];
@@ -220,10 +222,10 @@ __global__ void k_adj_vel(const AdjArgs<R> A)
 template <typename R>
 __global__ void k_adj_p(const AdjArgs<R> A)
 {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < A.vol;
-         i += (long long)gridDim.x * blockDim.x) {
-        Pt<R> P;
-        if (!decode(A, i, P)) continue;
+    Pt<R> P;
+    long long i;
+    if (!point(A, P, i)) return;
+    {
         R s = 0;
         for (int ax = 0; ax < 3; ++ax)
             if (A.ax_on[ax]) s += dminus(A, A.Gd[ax], i, P.c[ax], P.n[ax], P.st[ax]);
@@ -425,7 +427,7 @@ int gradient_impl(fw_medium *m, int n_steps, int K, const void *G, const void *a
     A.gk = static_cast<double *>(gacc.p);
     A.gs = static_cast<double *>(gacc.p) + vol;
     auto image = [&](int k) { return static_cast<const char *>(seg.p) + (size_t)k * SB; };
-    const int nb = nblocks((long long)vol);
+    const dim3 pgrid((unsigned)((m->NX + 255) / 256), (unsigned)m->NY, (unsigned)m->NZ);   // one thread per point
     const double inv_dxd = 1.0 / std::pow(m->dx, m->ndim);
 
     // ---- reverse sweep, one checkpoint segment at a time ----
@@ -458,9 +460,9 @@ int gradient_impl(fw_medium *m, int n_steps, int K, const void *G, const void *a
                     A.fpsi1[q][ax] = m->psi1[q][ax] ? reinterpret_cast<const R *>(F + off(m->psi1[q][ax])) : nullptr;
             }
             for (int q = 0; q < m->nmech; ++q) A.fpsi2[q] = reinterpret_cast<const R *>(F + off(m->psi2[q]));
-            k_adj_pres<R><<<nb, 256, 0, s>>>(A);
-            k_adj_vel<R><<<nb, 256, 0, s>>>(A);
-            k_adj_p<R><<<nb, 256, 0, s>>>(A);
+            k_adj_pres<R><<<pgrid, 256, 0, s>>>(A);
+            k_adj_vel<R><<<pgrid, 256, 0, s>>>(A);
+            k_adj_p<R><<<pgrid, 256, 0, s>>>(A);
         }
         ADJ_CK(cudaGetLastError());
     }
@@ -505,6 +507,7 @@ extern "C" int fw_gradient(fw_medium *m, int n_steps, int checkpoint_every, cons
     if (m->sticky) return m->sticky;
     if (m->nonlinear) return FW_ERR_UNSUPPORTED;
     if (m->storage != FW_STORE_F32 && m->storage != FW_STORE_F64) return FW_ERR_UNSUPPORTED;
+    if (m->NY > 65535 || m->NZ > 65535) return FW_ERR_UNSUPPORTED;   // launch grid's y and z limits
     int K = checkpoint_every > 0 ? checkpoint_every : std::max(1, (int)std::lround(std::sqrt((double)n_steps)));
     K = std::min(K, n_steps);
     cudaStream_t s = (cudaStream_t)stream;
