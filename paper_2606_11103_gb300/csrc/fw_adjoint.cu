@@ -141,13 +141,15 @@ __global__ void k_adj_pres(const AdjArgs<R> A)
         const R ce = t[3] + (r - R(1)) * t[kLutDk + 1];   // the forward sweep's ceff
         R stp = div * ce;
         R ldiv = ce * lst;
-        double gs = 0.0;
+        // this step's terms in the working precision; the sum over steps in FP64
+        // (FP64 arithmetic is slow on this GPU: one addition per point and step)
+        R gs = 0;
         for (int m = 0; m < A.nmech; ++m) {
             const R old = A.fpsi2[m][i];
             stp += t[kLutH2 + m] * old;
             const R ln = A.lpsi2[m][i];
             ldiv += r * t[kLutA2 + m] * ln;
-            gs += double(dtb[12 + m] * old + r * dtb[8 + m] * div) * double(ln + R(0.5) * lst);
+            gs += (dtb[12 + m] * old + r * dtb[8 + m] * div) * (ln + R(0.5) * lst);
             A.lpsi2[m][i] = t[kLutB2 + m] * ln + t[kLutH2 + m] * lst;
         }
         for (int ax = 0; ax < 3; ++ax) {
@@ -167,8 +169,8 @@ __global__ void k_adj_pres(const AdjArgs<R> A)
             }
             A.Q[ax][i] = qv;
         }
-        A.gk[i] += -double(stp) * double(lp);
-        A.gs[i] += gs;
+        A.gk[i] += double(-stp * lp);
+        A.gs[i] += double(gs);
     }
 }
 
@@ -184,7 +186,7 @@ __global__ void k_adj_vel(const AdjArgs<R> A)
         const R own = A.rho[i];
         const R r = cell_ramp(A, P);
         const R ce = t[2] + (r - R(1)) * t[kLutDk];
-        double gs = 0.0;
+        R gs = 0;   // this step's terms; the sum over steps in FP64
         for (int ax = 0; ax < 3; ++ax) {
             if (!A.ax_on[ax]) continue;
             const int c = P.c[ax], n = P.n[ax];
@@ -199,7 +201,7 @@ __global__ void k_adj_vel(const AdjArgs<R> A)
                 const R old = A.fpsi1[m][ax][i];
                 const R ln = A.lpsi1[m][ax][i];
                 lg += r * t[kLutA1 + m] * ln;
-                gs += double(dtb[4 + m] * old + r * dtb[m] * g) * double(ln + R(0.5) * lst);
+                gs += (dtb[4 + m] * old + r * dtb[m] * g) * (ln + R(0.5) * lst);
                 A.lpsi1[m][ax][i] = t[kLutB1 + m] * ln + t[kLutH1 + m] * lst;
             }
             if (A.pdh[ax]) {
@@ -215,7 +217,7 @@ __global__ void k_adj_vel(const AdjArgs<R> A)
             A.Gd[ax][i] = lg;
             A.lv[ax][i] = lv;
         }
-        A.gs[i] += gs;
+        A.gs[i] += double(gs);
     }
 }
 
