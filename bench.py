@@ -11,8 +11,13 @@ sweep, sources, receivers).  Metric: voxel-updates per second (Gvox/s, one
 voxel advanced by one full time step).  The working set (~15 GB) is far
 larger than L2, so no flush is needed between steps.
 
+Other workloads: ``--workload twolayer2d`` (2D two-layer nonlinear medium,
+2048^2), ``--workload serving`` (a stream of mixed 2D/3D requests through the
+continuous-batching server: throughput, p50/p99 latency) and ``--workload
+adjoint`` (whole gradients of a receiver functional on a 1024^2 medium).
+
 Prints ONE JSON line on rank 0.  ``--impl reference`` times the FP64 CPU
-oracle (the reference arm of this build) on a crop of the same workload.
+oracle (the paper ships no runnable code) on a crop of the same workload.
 """
 from __future__ import annotations
 

@@ -1,4 +1,4 @@
-"""Simulation-based weight selection on the GPU (Sec. 3.2; SURVEY f1):
+"""Simulation-based weight selection on the GPU (Sec. 3.2):
 calibrate.py simulates every weight's relaxation set in the Sec. 4.1-4.2
 protocol and keeps the lowest simulated attenuation NRMSE.
 
