@@ -45,3 +45,24 @@ def test_spectral_measurement_recovers_a_prescribed_medium(f0):
     c = w * d / (phi + 2 * math.pi * k)
     assert np.allclose(-np.log(ratio) / d, cal.alpha_target(a0, y, fb), rtol=1e-6, atol=0)
     assert np.allclose(c, cal.phase_velocity_target(a0, y, fb, c0), rtol=1e-9, atol=0)
+
+
+def test_selection_rule(monkeypatch):
+    """Lowest simulated NRMSE wins, the dispersion error breaks ties, a
+    candidate whose run went unstable is never kept, and the calibration is
+    labelled failed above 10 % NRMSE or 5 m/s (Sec. 3.2)."""
+    table = {"a": (0.020, 3.0), "b": (0.010, 4.0), "c": (0.010, 1.0), "d": None}
+
+    def fake(p, alpha0, y, c0=1540.0, **kw):
+        if table[p] is None:
+            raise RuntimeError("unstable")
+        return {"nrmse": table[p][0], "disp_rmse": table[p][1]}
+
+    monkeypatch.setattr(cal, "simulated_accuracy", fake)
+    best, scores, failed = cal.select_weight(["a", "b", "c", "d"], 0.5, 1.0)
+    assert best == 2 and not failed
+    assert scores[3] == (math.inf, math.inf)
+    table.update(a=(0.12, 1.0), b=(0.11, 2.0), c=(0.2, 0.5))
+    assert cal.select_weight(["a", "b", "c"], 0.5, 1.0)[0:3:2] == (1, True)
+    table.update(a=(0.05, 6.0))
+    assert cal.select_weight(["a"], 0.5, 1.0)[2]
