@@ -119,7 +119,7 @@ __device__ __forceinline__ R cell_ramp(const AdjArgs<R> &A, const Pt<R> &P)
     return ramp_of(s, A.inv_lr);
 }
 
-template <typename R>
+template <typename R, int DIM, int NM>
 __global__ void k_adj_pres(const AdjArgs<R> A)
 {
     Pt<R> P;
@@ -129,8 +129,9 @@ __global__ void k_adj_pres(const AdjArgs<R> A)
         const R *t = A.lut + (size_t)A.cls[i] * kLutStride;
         const R *dtb = A.dlut + (size_t)A.cls[i] * kDStride;
         R q[3] = {0, 0, 0}, div = 0;
+#pragma unroll
         for (int ax = 0; ax < 3; ++ax)
-            if (A.ax_on[ax]) {
+            if (DIM == 3 || ax != 1) {
                 q[ax] = dminus(A, A.fv1[ax], i, P.c[ax], P.n[ax], P.st[ax]);
                 div += q[ax];
             }
@@ -144,7 +145,8 @@ __global__ void k_adj_pres(const AdjArgs<R> A)
         // this step's terms in the working precision; the sum over steps in FP64
         // (FP64 arithmetic is slow on this GPU: one addition per point and step)
         R gs = 0;
-        for (int m = 0; m < A.nmech; ++m) {
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
             const R old = A.fpsi2[m][i];
             stp += t[kLutH2 + m] * old;
             const R ln = A.lpsi2[m][i];
@@ -152,8 +154,9 @@ __global__ void k_adj_pres(const AdjArgs<R> A)
             gs += (dtb[12 + m] * old + r * dtb[8 + m] * div) * (ln + R(0.5) * lst);
             A.lpsi2[m][i] = t[kLutB2 + m] * ln + t[kLutH2 + m] * lst;
         }
+#pragma unroll
         for (int ax = 0; ax < 3; ++ax) {
-            if (!A.ax_on[ax]) continue;
+            if (DIM == 2 && ax == 1) continue;
             R qv = ldiv;
             if (A.pdi[ax]) {
                 const R d = A.pdi[ax][P.c[ax]];
@@ -174,7 +177,7 @@ __global__ void k_adj_pres(const AdjArgs<R> A)
     }
 }
 
-template <typename R>
+template <typename R, int DIM, int NM>
 __global__ void k_adj_vel(const AdjArgs<R> A)
 {
     Pt<R> P;
@@ -187,8 +190,9 @@ __global__ void k_adj_vel(const AdjArgs<R> A)
         const R r = cell_ramp(A, P);
         const R ce = t[2] + (r - R(1)) * t[kLutDk];
         R gs = 0;   // this step's terms; the sum over steps in FP64
+#pragma unroll
         for (int ax = 0; ax < 3; ++ax) {
-            if (!A.ax_on[ax]) continue;
+            if (DIM == 2 && ax == 1) continue;
             const int c = P.c[ax], n = P.n[ax];
             const long long st = P.st[ax];
             const R lv = A.lv[ax][i] - dplus(A, A.Q[ax], i, c, n, st);
@@ -197,7 +201,8 @@ __global__ void k_adj_vel(const AdjArgs<R> A)
             const R lst = -dtr * lv;
             const R g = dplus(A, A.fp, i, c, n, st);
             R lg = ce * lst;
-            for (int m = 0; m < A.nmech; ++m) {
+#pragma unroll
+            for (int m = 0; m < NM; ++m) {
                 const R old = A.fpsi1[m][ax][i];
                 const R ln = A.lpsi1[m][ax][i];
                 lg += r * t[kLutA1 + m] * ln;
@@ -221,7 +226,7 @@ __global__ void k_adj_vel(const AdjArgs<R> A)
     }
 }
 
-template <typename R>
+template <typename R, int DIM, int NM>
 __global__ void k_adj_p(const AdjArgs<R> A)
 {
     Pt<R> P;
@@ -229,8 +234,9 @@ __global__ void k_adj_p(const AdjArgs<R> A)
     if (!point(A, P, i)) return;
     {
         R s = 0;
+#pragma unroll
         for (int ax = 0; ax < 3; ++ax)
-            if (A.ax_on[ax]) s += dminus(A, A.Gd[ax], i, P.c[ax], P.n[ax], P.st[ax]);
+            if (DIM == 3 || ax != 1) s += dminus(A, A.Gd[ax], i, P.c[ax], P.n[ax], P.st[ax]);
         A.lp[i] -= s;
     }
 }
@@ -290,6 +296,36 @@ __global__ void k_grad_out(const double *uc, const double *us, const float *a0f,
                 g = a > 0.0 ? g / a : 0.0;
             }
             ga[j] = D(g);
+        }
+    }
+}
+
+// the three adjoint kernels of one reverse step, instantiated per dimension
+// and number of mechanisms (their loops unroll)
+template <typename R, int DIM, int NM>
+void launch_reverse_dn(const AdjArgs<R> &A, dim3 grid, cudaStream_t s)
+{
+    k_adj_pres<R, DIM, NM><<<grid, 256, 0, s>>>(A);
+    k_adj_vel<R, DIM, NM><<<grid, 256, 0, s>>>(A);
+    k_adj_p<R, DIM, NM><<<grid, 256, 0, s>>>(A);
+}
+
+template <typename R>
+void launch_reverse(const AdjArgs<R> &A, int ndim, int nmech, dim3 grid, cudaStream_t s)
+{
+    if (ndim == 2) {
+        switch (nmech) {
+        case 1: launch_reverse_dn<R, 2, 1>(A, grid, s); break;
+        case 2: launch_reverse_dn<R, 2, 2>(A, grid, s); break;
+        case 3: launch_reverse_dn<R, 2, 3>(A, grid, s); break;
+        default: launch_reverse_dn<R, 2, 4>(A, grid, s); break;
+        }
+    } else {
+        switch (nmech) {
+        case 1: launch_reverse_dn<R, 3, 1>(A, grid, s); break;
+        case 2: launch_reverse_dn<R, 3, 2>(A, grid, s); break;
+        case 3: launch_reverse_dn<R, 3, 3>(A, grid, s); break;
+        default: launch_reverse_dn<R, 3, 4>(A, grid, s); break;
         }
     }
 }
@@ -462,9 +498,7 @@ int gradient_impl(fw_medium *m, int n_steps, int K, const void *G, const void *a
                     A.fpsi1[q][ax] = m->psi1[q][ax] ? reinterpret_cast<const R *>(F + off(m->psi1[q][ax])) : nullptr;
             }
             for (int q = 0; q < m->nmech; ++q) A.fpsi2[q] = reinterpret_cast<const R *>(F + off(m->psi2[q]));
-            k_adj_pres<R><<<pgrid, 256, 0, s>>>(A);
-            k_adj_vel<R><<<pgrid, 256, 0, s>>>(A);
-            k_adj_p<R><<<pgrid, 256, 0, s>>>(A);
+            launch_reverse<R>(A, m->ndim, m->nmech, pgrid, s);
         }
         ADJ_CK(cudaGetLastError());
     }
