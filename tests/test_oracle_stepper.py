@@ -483,3 +483,74 @@ def test_tissue_ramp_keeps_the_absorbing_layer_stable(oracle_lib):
         out[ramp] = np.abs(sim.p).max() / peak
     assert out[True] < 1e-4, out
     assert out[False] > 1e3, out
+
+
+def _layer_wkb_db(n, l_t, l_b, r0, c, dx, f0):
+    """Round trip through the bottom absorbing layer in the WKB limit:
+    exp(-2 sum_cells a dx), a = -Im k of the layer's Debye mechanism on both
+    stretches (kappa = 1, lossless tissue), with the profile written out from
+    its definition: depth s from the inner edge (half points for the
+    gradient side, integer points for the divergence side), d(s) = 0.1 d_max
+    (s/L_T)^2 in the transition, d_max (0.1 + 0.9 ((s - L_T)/L_B)^2) beyond
+    (d_max (s/L_B)^2 without transition), d_max = -3 c ln(R0) / (2 L_B dx),
+    alpha(s) = pi f0 (1 - s/(L_T + L_B))."""
+    w = l_t + l_b
+    d_max = -3.0 * c * math.log(r0) / (2.0 * l_b * dx)
+    om = 2 * math.pi * f0
+    total = 0.0
+    for i in range(n - w - 1, n):
+        k = om / c
+        for s in (max(0.0, i + 0.5 - (n - w - 0.5)), max(0.0, i - (n - w - 0.5))):
+            if s <= 0:
+                d = 0.0
+            elif l_t > 0 and s <= l_t:
+                d = 0.1 * d_max * (s / l_t) ** 2
+            elif l_t > 0:
+                d = d_max * (0.1 + 0.9 * ((s - l_t) / l_b) ** 2)
+            else:
+                d = d_max * (s / l_b) ** 2
+            alpha = math.pi * f0 * (1.0 - s / w)
+            k = k / np.sqrt(1.0 - d / (d + alpha + 1j * om))      # stretch 1 - gamma, kappa = 1
+        total += -k.imag * dx
+    return 20.0 * math.log10(math.exp(-2.0 * total))
+
+
+@pytest.mark.parametrize("l_t,l_b,r0", [(0, 40, 1e-2), (0, 40, 1e-3), (24, 24, 1e-2)])
+def test_absorbing_layer_round_trip(l_t, l_b, r0, oracle_lib):
+    """Absorbing-profile constants (the reading of Sec. 4.3's C-PML): a 1 MHz
+    plane wave crosses the bottom layer, meets the zero field beyond the grid
+    and crosses back.  Its amplitude at f0, against the same run on a much
+    deeper grid, equals the WKB round trip of the profile to 1.5 dB, and a
+    layer without transition returns the design reflection R0 to 1 dB."""
+    c, rho, f0, ppw = 1540.0, 1000.0, 1e6, 16
+    dx = c / (f0 * ppw)
+    dt = 0.2 * dx / c
+    w = l_t + l_b
+    src_off, depth = 300, 340
+
+    def run(extra):
+        shape = (w + src_off + depth + extra + w, 4)
+        med = OracleMedium(shape, dx, dt, np.full(shape, c), np.full(shape, rho), np.zeros(shape, np.int64),
+                           [fit.RelaxParams.lossless(1)], pml=l_b, transition=l_t, f0=f0, R0=r0,
+                           periodic=(False, True))
+        sim = OracleSim(med)
+        src = np.zeros(shape, np.uint8)
+        src[w + src_off] = 1
+        rcv = np.zeros(shape, np.uint8)
+        rcv[w + src_off + depth - 20, 0] = 1
+        nt = int((depth + 2 * (20 + w) + 200) / 0.2)
+        sim.set_sources(src, gaussian_pulse(f0, dt, nt, 1.0, tau=3.0 / f0)[None])
+        sim.set_receivers(rcv, nt)
+        sim.run(nt)
+        return sim.traces[0], shape[0]
+
+    near, n = run(0)
+    far, _ = run(2000)
+    N = 1 << 16
+    f = np.fft.rfftfreq(N, dt)
+    k0 = int(np.argmin(np.abs(f - f0)))
+    got = 20 * math.log10(abs(np.fft.rfft(near - far, N)[k0]) / abs(np.fft.rfft(far, N)[k0]))
+    want = _layer_wkb_db(n, l_t, l_b, r0, c, dx, f0)
+    assert abs(got - want) < 1.5, (got, want)
+    if l_t == 0:
+        assert abs(got - 20 * math.log10(r0)) < 1.0, got
