@@ -165,3 +165,15 @@ def test_fit_lossless_and_threads(L):
     p1, r1 = fw.fit_relaxation(0.4, 1.2, 2, maxiter=500, n_threads=1)
     p4, r4 = fw.fit_relaxation(0.4, 1.2, 2, maxiter=500, n_threads=4)
     assert r1.J == r4.J and r1.w == r4.w
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """No fallback path: loading from a path without the library raises."""
+    from paper_2606_11103_gb300 import _lib
+    saved = _lib._lib
+    try:
+        _lib._lib = None
+        with pytest.raises(RuntimeError, match="not built"):
+            _lib.load(str(tmp_path / "libfullwave_gb.so"))
+    finally:
+        _lib._lib = saved
