@@ -143,7 +143,8 @@ void fw_fit_default_opts(fw_fit_opts *opts);
  * weight with the lowest attenuation NRMSE kept (dispersion error breaks
  * ties).  alpha0 = 0 returns the lossless set (d = 0, kappa = 1) without
  * fitting.  opts may be NULL (defaults).  Errors: FW_ERR_ARG for n_mech
- * outside 1..4, alpha0 < 0, y outside [0.1, 3], or bad opts.  A poor fit is
+ * outside 1..4, alpha0 < 0, y outside the paper's valid range [0.4, 2.0]
+ * (abstract, Sec. 3.1) when alpha0 > 0, or bad opts.  A poor fit is
  * not an error: rep->failed is set.  rep may be NULL.  Blocking; thread-safe. */
 int fw_fit_relaxation(double alpha0, double y, int n_mech, const fw_fit_opts *opts,
                       fw_relax_params *out, fw_fit_report *rep);
@@ -153,6 +154,17 @@ int fw_fit_relaxation(double alpha0, double y, int n_mech, const fw_fit_opts *op
  * log10 a2] (2 + 4N doubles).  For inspection and tests. */
 int fw_fit_objective(double alpha0, double y, double w, const fw_fit_opts *opts,
                      const double *theta, int n_mech, double *J);
+
+/* The calibration's targets at n frequencies f_hz (host arrays): the
+ * power-law attenuation alpha0 f^y in Np/m (Eq. power_law_attenuation,
+ * alpha0 in dB/(MHz^y cm)) into alpha, and the phase velocity of its
+ * Kramers-Kronig pair (Eq. kk_relation) with c(f_ref) = c0 into c_phase
+ * (m/s); |y - 1| < 1e-6 takes the logarithmic limit of the relation.  The
+ * same arithmetic as the fit's objective.  Errors: FW_ERR_ARG (alpha0 < 0,
+ * c0 or f_ref not positive, a frequency not positive, y outside [0.4, 2.0]
+ * when alpha0 > 0, NULL arrays). */
+int fw_fit_targets(double alpha0, double y, double c0, double f_ref, const double *f_hz, int n,
+                   double *alpha, double *c_phase);
 
 /* Model complex wavenumber of Eq. dispersion_relations for a parameter set
  * and medium speed c at n frequencies f_hz: writes Re k and Im k (attenuation
@@ -177,7 +189,9 @@ void fw_set_allocator(void *(*alloc)(size_t bytes, void *ctx),
                       void (*release)(void *ptr, void *ctx), void *ctx);
 
 /* Device bytes a medium of this grid needs (state, maps, tables; not the
- * source/receiver buffers).  For admission control. */
+ * source/receiver buffers): the fields and memory variables of Sec. 2.1
+ * (Eqs. wave1, wave2, relaxation4), the absorbing-layer memory of Sec. 4.6
+ * and the per-voxel maps.  For admission control.  Errors: FW_ERR_ARG. */
 int fw_medium_bytes(const fw_grid *g, int n_mech, int storage, int nonlinear, size_t *bytes);
 
 /* Build a medium from per-voxel maps (Sec. 2.1, Sec. 4.6): every distinct
@@ -187,8 +201,8 @@ int fw_medium_bytes(const fw_grid *g, int n_mech, int storage, int nonlinear, si
  * class's voxels.  c, rho, alpha0, y: host or device float arrays of
  * nx*ny*nz values; beta may be NULL (linear).  The rest is as in
  * fw_create_medium_classes.
- * Errors: FW_ERR_ARG (non-positive c or rho, y outside [0.1, 3] where
- * alpha0 > 0, more than 65535 classes, CFL above the stability limit),
+ * Errors: FW_ERR_ARG (non-positive c or rho, y outside the valid range
+ * [0.4, 2.0] (abstract, Sec. 3.1) where alpha0 > 0, more than 65535 classes, CFL above the stability limit),
  * FW_ERR_NOMEM, FW_ERR_CUDA.  Blocking (returns when the medium is ready). */
 int fw_create_medium(const fw_grid *g, const float *c, const float *rho, const float *beta,
                      const float *alpha0, const float *y, int n_mech, int storage,
@@ -204,7 +218,9 @@ int fw_create_medium_classes(const fw_grid *g, const float *c, const float *rho,
                              const fw_relax_params *classes, int n_classes, int storage,
                              void *stream, fw_medium **out);
 
-/* Sources (additive volume sources on p): mask (host, uint8, nx*ny*nz)
+/* Sources (the volume source of the simulation protocol, Sec. 4.1: an
+ * additive source on p, one step of the pressure update's K dt per unit
+ * volume rate, Eq. wave2): mask (host, uint8, nx*ny*nz)
  * selects cells in C order; waveforms (host, n_wave x n_steps floats, volume
  * rate [m^D/s]); wave_of_src (host, one int per source in mask order) picks
  * a waveform row, or NULL: one shared row (n_wave = 1) or one row per source
@@ -219,16 +235,23 @@ int fw_create_medium_classes(const fw_grid *g, const float *c, const float *rho,
 int fw_set_sources(fw_medium *m, const uint8_t *mask, const float *waveforms, int n_wave,
                    int n_steps, const int32_t *wave_of_src);
 
-/* Receivers: mask (host, uint8) selects cells in C order; time step `it`
+/* Receivers (the pressure traces the measurements of Sec. 4.1-4.3 are
+ * taken from): mask (host, uint8) selects cells in C order; time step `it`
  * records p after the source into column it/decim when it % decim == 0, for
  * it < n_steps.  Traces are [n_rcv][ceil(n_steps/decim)] and are zeroed. */
 int fw_set_receivers(fw_medium *m, const uint8_t *mask, int decim, int n_steps);
 
-/* Advance n_steps time steps on stream with plain kernel launches. */
+/* Advance n_steps time steps on stream with plain kernel launches: one step
+ * is the velocity half step (Eqs. wave1, relaxation4, relaxation_psi on the
+ * gradient side), the pressure half step (Eqs. wave2, relaxation4,
+ * relaxation_psi on the divergence side; absorbing mechanism of Sec. 2.1 /
+ * Sec. 4.6), then sources and receivers, on the staggered grid of Sec. 3.3.
+ * Errors: FW_ERR_ARG, FW_ERR_CUDA, or the medium's sticky error. */
 int fw_step(fw_medium *m, int n_steps, void *stream);
 
-/* Advance n_steps time steps on stream through cached CUDA graphs of fixed
- * step chunks (the fast path; same results as fw_step). */
+/* Advance n_steps time steps (the same step as fw_step, Sec. 2.1 / 3.3) on
+ * stream through cached CUDA graphs of fixed step chunks (the fast path;
+ * bitwise the same results as fw_step).  Errors as fw_step. */
 int fw_run(fw_medium *m, int n_steps, void *stream);
 
 /* fw_step with a CUDA event around each sweep: advances n_steps on stream
@@ -252,8 +275,13 @@ int fw_set_waveform_samples(fw_medium *m, int it0, int n, const float *samples, 
  * dst.  For streaming results step by step. */
 int fw_read_receivers_range(fw_medium *m, int col0, int ncol, void *dst, void *stream);
 
-/* Copy a field to dst (host or device), unpadded C order, as float
- * (as_f64 = 0) or double (as_f64 = 1).  Ordered on stream; blocking. */
+/* Copy a field of the state of Sec. 2.1 (p, v_d, the memory variables psi of
+ * Eq. relaxation4, the absorbing-layer memory) to dst (host or device),
+ * unpadded C order, as float (as_f64 = 0) or double (as_f64 = 1); 16-bit
+ * memory variables come back in the units of the FP32 ones.  Ordered on
+ * stream; blocking.  Device memory: one staging buffer of the field's size
+ * from the installed allocator.  Errors: FW_ERR_ARG (field, idx, pointer),
+ * FW_ERR_NOMEM, FW_ERR_CUDA. */
 int fw_read_field(fw_medium *m, int which, int idx, void *dst, int as_f64, void *stream);
 
 /* fw_read_field without any device allocation.  No counterpart in the
@@ -264,13 +292,18 @@ int fw_read_field(fw_medium *m, int which, int idx, void *dst, int as_f64, void 
  * cudaMalloc/cudaFree synchronise the device.
  * Same arguments, layout and result as fw_read_field, but the copy is staged
  * in one device array of FW_NOALLOC_MAX_BYTES bytes that the library defines
- * at file scope: every device that loads the library holds that array until
- * the process exits, and no call allocates or frees device memory.
+ * at file scope, and no call allocates or frees device memory.  CUDA loads
+ * device code lazily, so the array takes its device memory when the library
+ * first looks up its address on a device: every fw_create_medium* does that
+ * for the medium's device before it returns, so the array is resident from
+ * the first medium on (before the caller hands the rest of the device to a
+ * pool) and stays until the process exits.
  * - Limit: nx*ny*nz*(as_f64 ? 8 : 4) <= FW_NOALLOC_MAX_BYTES (64 MiB, e.g.
  *   a 256^3 float field), else FW_ERR_SIZE and nothing is copied.
- * - The first call on a device looks up the array's device address (with
- *   that device current), so make that first call before any stream capture
- *   on the device.  The medium's device must be current.
+ * - The address lookup happens outside any stream capture (at medium
+ *   creation); should it have failed there, the first call on the device
+ *   repeats it, so make that call before any capture.  The medium's device
+ *   must be current.
  * - All calls share the one array and it keeps the last call's contents:
  *   calls whose work overlaps on the GPU (other streams, other host threads)
  *   race on it and must be ordered by the caller.  Blocking, like
@@ -326,7 +359,8 @@ int fw_load_state(fw_medium *m, const void *src, void *stream);
 int fw_gradient(fw_medium *m, int n_steps, int checkpoint_every, const void *G, const void *alpha0,
                 void *grad_c, void *grad_alpha0, int as_f64, void *stream);
 
-/* Stability monitor (non-finite pressure, Sec. 4.6): synchronises the
+/* Stability monitor (the divergence of long runs counted in Sec. 4.6 and
+ * Sec. 5.5: non-finite pressure): synchronises the
  * medium's last stream and returns FW_OK or FW_ERR_UNSTABLE (sticky);
  * max_abs_p (may be NULL) receives max |p| seen since creation. */
 int fw_status(fw_medium *m, float *max_abs_p);

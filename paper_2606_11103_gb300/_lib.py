@@ -96,6 +96,7 @@ SIGNATURES = {
     "fw_fit_relaxation": (_I, [C.c_double, C.c_double, _I, C.POINTER(fw_fit_opts),
                                C.POINTER(fw_relax_params), C.POINTER(fw_fit_report)]),
     "fw_fit_objective": (_I, [C.c_double, C.c_double, C.c_double, C.POINTER(fw_fit_opts), _D, _I, _D]),
+    "fw_fit_targets": (_I, [C.c_double, C.c_double, C.c_double, C.c_double, _D, _I, _D, _D]),
     "fw_model_wavenumber": (_I, [C.POINTER(fw_relax_params), C.c_double, _D, _I, _D, _D]),
     "fw_nelder_mead": (_I, [_I, _D, _D, _D, OBJFN, _P, _I, C.c_double, C.c_double, _D,
                             C.POINTER(_I), C.POINTER(_I)]),

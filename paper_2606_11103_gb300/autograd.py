@@ -16,10 +16,18 @@ Two ways to build the medium:
 The gradient with respect to alpha0 follows the library's reading: the d of
 a voxel's mechanisms scale with alpha0(x) / alpha0_class (kappa and alpha
 fixed); see fw_gradient.
+
+Lifetime: the forward keeps its medium (device memory) for the backward.
+The backward runs once (``once_differentiable``): it releases the medium,
+and a second backward through the same graph (retain_graph=True) raises.  A
+forward whose inputs need no gradient releases its medium at once; one whose
+backward never runs releases it when autograd frees the graph (the Medium's
+finaliser).
 """
 from __future__ import annotations
 
 import torch
+from torch.autograd.function import once_differentiable
 
 from . import Medium
 
@@ -50,15 +58,22 @@ class FullwaveSim(torch.autograd.Function):
         start = m.save_state()
         m.run(setup["n_steps"])
         traces = torch.as_tensor(m.receivers(f64=f64)).to(dev)
+        if not (c.requires_grad or alpha0.requires_grad):
+            m.close()                 # nothing can call backward: release the device memory now
+            m = None
         ctx.medium, ctx.start, ctx.setup, ctx.f64 = m, start, setup, f64
         ctx.dtypes = (c.dtype, alpha0.dtype)
         ctx.save_for_backward(alpha0)
         return traces
 
     @staticmethod
+    @once_differentiable
     def backward(ctx, grad_traces):
         (alpha0,) = ctx.saved_tensors
         m, setup = ctx.medium, ctx.setup
+        if m is None:
+            raise RuntimeError("FullwaveSim.backward runs once per forward: the first backward released the "
+                               "medium; run the forward again for another gradient")
         dt = torch.float64 if ctx.f64 else torch.float32
         m.load_state(ctx.start)
         gc = torch.empty(setup["shape"], dtype=dt, device=grad_traces.device)

@@ -27,25 +27,34 @@ import math
 import numpy as np
 
 CENTRES = tuple(float(f) for f in np.arange(1e6, 20.01e6, 2.71e6))
-DB_PER_NP = 20.0 / math.log(10.0)
+
+
+def _targets(alpha0, y, f_hz, c0=1540.0, f_ref=1e6):
+    """(alpha0 f^y [Np/m], Kramers-Kronig phase velocity [m/s]) at f_hz from
+    the library's fw_fit_targets (the fit's own arithmetic)."""
+    import ctypes as C
+
+    from . import _lib
+
+    f = np.ascontiguousarray(np.atleast_1d(np.asarray(f_hz, np.float64)))
+    al, cp = np.empty_like(f), np.empty_like(f)
+    P = C.POINTER(C.c_double)
+    _lib.check(_lib.load().fw_fit_targets(float(alpha0), float(y), float(c0), float(f_ref), f.ctypes.data_as(P),
+                                          int(f.size), al.ctypes.data_as(P), cp.ctypes.data_as(P)),
+               "fw_fit_targets")
+    shape = np.shape(f_hz)
+    return al.reshape(shape), cp.reshape(shape)
 
 
 def alpha_target(alpha0, y, f_hz):
-    """alpha0 f^y in Np/m (alpha0 in dB/(MHz^y cm))."""
-    return alpha0 * (np.asarray(f_hz, np.float64) / 1e6) ** y * 100.0 / DB_PER_NP
+    """alpha0 f^y in Np/m (alpha0 in dB/(MHz^y cm)), Eq. power_law_attenuation."""
+    return _targets(alpha0, y, f_hz)[0]
 
 
 def phase_velocity_target(alpha0, y, f_hz, c0, f_ref=1e6):
     """c(w) of the power law through the Kramers-Kronig relation (Eq.
     kk_relation), c(f_ref) = c0; the y = 1 case takes its logarithmic limit."""
-    w = 2.0 * math.pi * np.asarray(f_hz, np.float64)
-    w0 = 2.0 * math.pi * f_ref
-    a = alpha0 * 100.0 / DB_PER_NP / (2.0 * math.pi * 1e6) ** y      # Np/m per (rad/s)^y
-    if abs(y - 1.0) < 1e-6:
-        inv_c = 1.0 / c0 - (2.0 / math.pi) * a * np.log(w / w0)
-    else:
-        inv_c = 1.0 / c0 + a * math.tan(math.pi * y / 2.0) * (w ** (y - 1.0) - w0 ** (y - 1.0))
-    return 1.0 / inv_c
+    return _targets(alpha0, y, f_hz, c0, f_ref)[1]
 
 
 def gaussian_pulse(f0, dt, n, amp=1.0):

@@ -19,6 +19,7 @@ cudaError_t sweeps_f16(const fw_medium *m, cudaStream_t s, int which);
 cudaError_t sweeps_f64(const fw_medium *m, cudaStream_t s, int which);
 cudaError_t io_f32(const fw_medium *m, int j, cudaStream_t s);
 cudaError_t io_f64(const fw_medium *m, int j, cudaStream_t s);
+void noalloc_prepare();
 }  // namespace fwgb
 
 using namespace fwgb;
@@ -689,6 +690,7 @@ int create_common(const fw_grid *g, const float *c, const float *rho, const floa
     if (cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking) != cudaSuccess) { release(m); return FW_ERR_CUDA; }
     if (launch_sweep(m, s, 4) != cudaSuccess) { release(m); return FW_ERR_CUDA; }
     if (cudaStreamSynchronize(s) != cudaSuccess) { release(m); return FW_ERR_CUDA; }
+    noalloc_prepare();
     m->last_stream = s;
     *out = m;
     return FW_OK;
@@ -825,7 +827,7 @@ int fw_create_medium(const fw_grid *g, const float *c, const float *rho, const f
     std::vector<size_t> ccount;
     for (size_t i = 0; i < n; ++i) {
         if (!(ha[i] >= 0.0f) || !std::isfinite(ha[i])) return FW_ERR_ARG;
-        if (ha[i] > 0.0f && !(hy[i] >= 0.1f && hy[i] <= 3.0f)) return FW_ERR_ARG;
+        if (ha[i] > 0.0f && !(hy[i] >= 0.4f && hy[i] <= 2.0f)) return FW_ERR_ARG;   // valid y range (abstract, Sec. 3.1)
         float yy = ha[i] > 0.0f ? hy[i] : 0.0f;
         unsigned int ua, uy;
         std::memcpy(&ua, &ha[i], 4);

@@ -25,6 +25,8 @@ namespace fwgb {
 namespace {
 using cd = std::complex<double>;
 constexpr double kPi = 3.14159265358979323846;
+// valid range of the power-law exponent (abstract, Sec. 3.1)
+constexpr double kYMin = 0.4, kYMax = 2.0;
 
 double db_per_neper() { return 20.0 / std::log(10.0); }
 
@@ -34,23 +36,32 @@ struct Band {
     double range_re = 0, range_im = 0;
 };
 
+// Power-law attenuation alpha0 f^y in Np/m (Eq. power_law_attenuation) and
+// the reciprocal phase velocity of its Kramers-Kronig pair (Eq. kk_relation)
+// at frequency f [Hz], with 1/c(2 pi f_ref) = 1/c0; |y - 1| < 1e-6 takes the
+// logarithmic limit of the relation.
+void power_law_target(double alpha0, double y, double c0, double f_ref, double f, double *alpha, double *inv_c)
+{
+    const double a0p = alpha0 * 100.0 / db_per_neper() / std::pow(2.0 * kPi * 1e6, y);
+    const double w0 = 2.0 * kPi * f_ref, om = 2.0 * kPi * f;
+    *alpha = alpha0 * std::pow(f / 1e6, y) * 100.0 / db_per_neper();
+    if (std::fabs(y - 1.0) < 1e-6)
+        *inv_c = 1.0 / c0 - (2.0 / kPi) * a0p * std::log(om / w0);
+    else
+        *inv_c = 1.0 / c0 + a0p * std::tan(kPi * y / 2.0) * (std::pow(om, y - 1.0) - std::pow(w0, y - 1.0));
+}
+
 Band make_band(double alpha0, double y, const fw_fit_opts &o)
 {
     Band b;
     const int n = o.n_freq;
     const double l0 = std::log10(o.f_min), l1 = std::log10(o.f_max);
-    const double a0p = alpha0 * 100.0 / db_per_neper() / std::pow(2.0 * kPi * 1e6, y);
-    const double w0 = 2.0 * kPi * o.f_ref;
     b.f.resize(n); b.om.resize(n); b.alpha.resize(n); b.inv_c.resize(n); b.k.resize(n);
     for (int j = 0; j < n; ++j) {
         double f = n > 1 ? std::pow(10.0, l0 + (l1 - l0) * j / (n - 1)) : o.f_min;
         double om = 2.0 * kPi * f;
-        double al = alpha0 * std::pow(f / 1e6, y) * 100.0 / db_per_neper();
-        double ic;
-        if (std::fabs(y - 1.0) < 1e-6)
-            ic = 1.0 / o.c0 - (2.0 / kPi) * a0p * std::log(om / w0);
-        else
-            ic = 1.0 / o.c0 + a0p * std::tan(kPi * y / 2.0) * (std::pow(om, y - 1.0) - std::pow(w0, y - 1.0));
+        double al, ic;
+        power_law_target(alpha0, y, o.c0, o.f_ref, f, &al, &ic);
         b.f[j] = f; b.om[j] = om; b.alpha[j] = al; b.inv_c[j] = ic;
         b.k[j] = cd(om * ic, -al);
     }
@@ -342,7 +353,10 @@ void parallel_for(int n_jobs, int n_threads, const std::function<void(int)> &fn)
 
 int fit_check(double alpha0, double y, int n_mech, const fw_fit_opts &o)
 {
-    if (n_mech < 1 || n_mech > FW_MAX_MECH || !(alpha0 >= 0.0) || !(y >= 0.1 && y <= 3.0)) return FW_ERR_ARG;
+    // the valid range of the power law, y in [0.4, 2.0] (abstract, Sec. 3.1);
+    // y does not enter a lossless (alpha0 = 0) calibration
+    if (n_mech < 1 || n_mech > FW_MAX_MECH || !(alpha0 >= 0.0)) return FW_ERR_ARG;
+    if (alpha0 > 0.0 && !(y >= kYMin && y <= kYMax)) return FW_ERR_ARG;
     if (!opts_ok(o)) return FW_ERR_ARG;
     return FW_OK;
 }
@@ -389,6 +403,22 @@ int fw_fit_objective(double alpha0, double y, double w, const fw_fit_opts *opts,
     Band b = make_band(alpha0, y, o);
     Objective obj{&b, w, o.c0, n_mech};
     *J = obj(theta);
+    return FW_OK;
+}
+
+int fw_fit_targets(double alpha0, double y, double c0, double f_ref, const double *f_hz, int n,
+                   double *alpha, double *c_phase)
+{
+    if (!f_hz || n < 0 || (n > 0 && (!alpha || !c_phase)) || !(alpha0 >= 0.0) || !(c0 > 0.0) || !(f_ref > 0.0))
+        return FW_ERR_ARG;
+    if (alpha0 > 0.0 && !(y >= kYMin && y <= kYMax)) return FW_ERR_ARG;
+    for (int j = 0; j < n; ++j)
+        if (!(f_hz[j] > 0.0)) return FW_ERR_ARG;
+    for (int j = 0; j < n; ++j) {
+        double ic;
+        power_law_target(alpha0, y, c0, f_ref, f_hz[j], &alpha[j], &ic);
+        c_phase[j] = 1.0 / ic;
+    }
     return FW_OK;
 }
 

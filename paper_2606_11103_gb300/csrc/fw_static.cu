@@ -86,6 +86,19 @@ cudaError_t unpad(const fw_medium *m, const void *src, int kind, D *dst, double 
 
 }  // namespace
 
+namespace fwgb {
+// Called by every medium creation with the medium's device current: the
+// address lookup loads this file's module on the device (CUDA loads modules
+// lazily, at their first use), so the staging array is resident from the
+// first medium on, before a caller hands the rest of device memory to a
+// pool.  A failure here is not the medium's: the read reports it.
+void noalloc_prepare()
+{
+    void *p = nullptr;
+    if (stage_address(&p) != FW_OK) cudaGetLastError();
+}
+}  // namespace fwgb
+
 extern "C" int fw_read_field_noalloc(fw_medium *m, int which, int idx, void *dst, int as_f64, void *stream)
 {
     if (!m || !dst) return FW_ERR_ARG;

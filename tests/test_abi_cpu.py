@@ -66,6 +66,17 @@ def test_argument_errors_without_a_gpu(L):
     out, rep = fw.fw_relax_params(), fw.fw_fit_report()
     assert L.fw_fit_relaxation(0.5, 5.0, 2, C.byref(o), C.byref(out), C.byref(rep)) == fw.FW_ERR_ARG
     assert L.fw_fit_relaxation(0.5, 1.0, 0, C.byref(o), C.byref(out), C.byref(rep)) == fw.FW_ERR_ARG
+    # y outside the valid range [0.4, 2.0] of the power law (abstract, Sec. 3.1), for a lossy class only
+    for y in (0.39, 2.01):
+        assert L.fw_fit_relaxation(0.5, y, 2, C.byref(o), C.byref(out), C.byref(rep)) == fw.FW_ERR_ARG
+    assert L.fw_fit_relaxation(0.0, 3.0, 2, C.byref(o), C.byref(out), C.byref(rep)) == fw.FW_OK
+    f = np.array([1e6, 5e6])
+    al, cp = np.zeros(2), np.zeros(2)
+    P = C.POINTER(C.c_double)
+    args = (f.ctypes.data_as(P), 2, al.ctypes.data_as(P), cp.ctypes.data_as(P))
+    assert L.fw_fit_targets(0.5, 2.5, 1540.0, 1e6, *args) == fw.FW_ERR_ARG
+    assert L.fw_fit_targets(0.5, 1.1, -1.0, 1e6, *args) == fw.FW_ERR_ARG
+    assert L.fw_fit_targets(0.5, 1.1, 1540.0, 1e6, *args) == fw.FW_OK
 
 
 def test_medium_bytes_scale_with_grid(L):

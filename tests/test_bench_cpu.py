@@ -59,9 +59,14 @@ def test_traffic_dropped_when_kernels_change(bench, monkeypatch):
 
 
 @pytest.mark.parametrize("workload", ["voronoi3d", "twolayer2d"])
-def test_both_arms_print_the_same_config(bench, workload):
+def test_reference_arm_names_the_crop_it_runs(bench, workload):
+    """The reference arm's config names the crop the oracle runs and the
+    workload it is cut from; its voxel count is the crop's."""
     a = argparse.Namespace(workload=workload, size=512, storage="f32")
     gpu = bench.workload_config(a, "x", "single GPU")
-    ref = bench.workload_config(a, "y", "host threads")
-    for k in ("workload", "voxels", "storage"):
-        assert gpu[k] == ref[k]
+    ref = bench.reference_config(a)
+    crop = bench.ORACLE_CROP[workload]
+    assert ref["voxels"] == (crop ** 2 if workload == "twolayer2d" else crop ** 3)
+    assert ref["voxels"] < gpu["voxels"]
+    assert gpu["workload"] in ref["workload"] and bench.oracle_sample(workload) in ref["workload"]
+    assert ref["storage"] == "f64"

@@ -5,8 +5,9 @@ code that must not let cudaMalloc/cudaFree synchronise the device).
 
 The call stages through one fixed device array instead of a per-call
 buffer.  These tests call it through the C ABI and compare what it returns
-with fw_read_field on the same medium, on consecutive calls, and check that a
-field larger than the array is refused.  The file is named so that pytest
+with fw_read_field on the same medium, on consecutive calls, check that it
+asks the installed device allocator for nothing, and that a field larger
+than the array is refused before anything is written.  The file is named so that pytest
 collects it last."""
 import ctypes as C
 
@@ -80,6 +81,37 @@ def test_noalloc_read_reduced_precision_psi(fw):
         m.close()
 
 
+def test_noalloc_read_asks_no_allocator(fw):
+    """With an allocator installed that refuses every request and counts
+    them, fw_read_field fails with FW_ERR_NOMEM while the no-allocation read
+    returns the same values as before and the allocator is never asked."""
+    spec = config_c1(n=96, n_steps=40)
+    m = fw.Medium.from_classes(spec.shape, spec.dx, spec.maps["c"], spec.maps["rho"],
+                               np.zeros(spec.shape, np.uint16), [_lossy(fw, 2)], dt=spec.dt,
+                               pml=spec.pml, f0=spec.f0, stream=0)
+    m.set_sources(spec.src_mask, spec.src_waves)
+    m.step(40, stream=0)
+    want = m.read_field(0, 0, stream=0)
+    asked = []
+    ALLOC, FREE = fw._lib.ALLOCFN, fw._lib.FREEFN
+    refuse = ALLOC(lambda nbytes, ctx: asked.append(int(nbytes)) or None)
+    noop = FREE(lambda ptr, ctx: None)
+    lib = fw.lib()
+    lib.fw_set_allocator(refuse, noop, None)
+    try:
+        out = np.zeros(m.shape, np.float32)
+        rc = lib.fw_read_field(m.h, 0, 0, C.c_void_p(out.ctypes.data), 0, C.c_void_p(0))
+        assert rc == fw._lib.FW_ERR_NOMEM and len(asked) == 1
+        for _ in range(2):
+            rc, got = _noalloc(fw, m, 0, 0, False)
+            assert rc == 0, fw.FwError(rc)
+            assert np.array_equal(got, want)
+        assert len(asked) == 1
+    finally:
+        lib.fw_set_allocator(ALLOC(), FREE(), None)
+    m.close()
+
+
 def test_noalloc_read_refuses_fields_above_the_limit(fw):
     limit = fw._lib.FW_NOALLOC_MAX_BYTES
     n = int(np.ceil(np.sqrt(limit / 8 + 1)))            # n^2 doubles just above the limit
@@ -87,9 +119,10 @@ def test_noalloc_read_refuses_fields_above_the_limit(fw):
     one = np.ones(shape, np.float32)
     m = fw.Medium.from_classes(shape, 1e-4, one * 1540, one * 1000, np.zeros(shape, np.uint16),
                                [fw.relax_params(1, 1, [0], [1e9], [0], [1e9])], dt=2e-8, stream=0)
-    out = np.zeros(1, np.float64)                      # never written: the call must refuse first
+    out = np.full(shape, -7.0, np.float64)             # a full-size buffer, left as it was
     rc = fw.lib().fw_read_field_noalloc(m.h, 0, 0, C.c_void_p(out.ctypes.data), 1, C.c_void_p(0))
     assert rc == fw._lib.FW_ERR_SIZE
+    assert np.all(out == -7.0)
     assert fw.lib().fw_strerror(rc)
     rc, got = _noalloc(fw, m, 0, 0, False)             # the float read of the same field fits
     assert rc == 0 and np.array_equal(got, m.read_field(0, 0, stream=0))
