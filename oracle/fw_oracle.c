@@ -23,6 +23,16 @@
  * Discretisation (Sec. 3.3): staggered grid, p at integer points and times,
  * v_d at half points along d and half times; first derivatives of 2M = 8th
  * order with the Taylor staggered coefficients; second-order leapfrog in time.
+ * Optionally (Sec. 3.3: 2M-th order in space, fourth order in time, after Tan
+ * & Huang, J. Comput. Phys. 276 (2014)) every first derivative takes the
+ * time-space stencil of that method instead: with per-point coefficients
+ * a_m, b (chosen by the caller from the point's r = c dt / dx, see
+ * oracle/medium.py),
+ *   D f = (1/dx) [ sum_m a_m (f(+m) - f(-m+1)) along d
+ *                + b sum over the other axes e and s = +-1 of the two-point
+ *                  difference along d of f shifted by s along e ],
+ * the coefficients of a velocity point being those of its cell (the lower
+ * neighbour), like its relaxation class.
  * Time index of Eq. relaxation_psi, taken literally: the memory variable
  * lives half a step away from the derivative that drives it, so the
  * derivative g computed in a half step is the midpoint input that advances
@@ -70,6 +80,7 @@ typedef struct {
     const double *a2[ORC_MAXMECH][3], *b2[ORC_MAXMECH][3];   /* at p points, per d */
     const double *a1p[3], *b1p[3];   /* absorbing mechanism at v_d points, or NULL */
     const double *a2p[3], *b2p[3];   /* absorbing mechanism at p points, or NULL */
+    const double *tha[4], *thb;      /* time-space stencil per cell, or NULL (Taylor weights) */
 } orc_coeffs;
 
 typedef struct {
@@ -102,29 +113,60 @@ static double at(const orc_coeffs *g, const double *f, size_t base, int d, int c
     return f[base + ((ptrdiff_t)c - c0) * (ptrdiff_t)stride(g, d)];
 }
 
-/* Forward staggered derivative of p along d, at the v_d point c+1/2. */
-static double dplus(const orc_coeffs *g, const double *p, int i0, int i1, int i2, int d)
+/* Value of f at the point (i0, i1, i2) moved by s along axis e and by t
+ * along axis d; zero outside the grid unless the axis is periodic. */
+static double at2(const orc_coeffs *g, const double *f, const int *idx, int e, int s, int d, int t)
+{
+    int c[3] = {idx[0], idx[1], idx[2]};
+    c[e] += s;
+    c[d] += t;
+    for (int ax = 0; ax < 3; ++ax) {
+        int n = g->n[ax];
+        if (c[ax] < 0 || c[ax] >= n) {
+            if (!g->periodic[ax]) return 0.0;
+            c[ax] = ((c[ax] % n) + n) % n;
+        }
+    }
+    return f[((size_t)c[2] * g->n[1] + c[1]) * g->n[0] + c[0]];
+}
+
+/* Staggered derivative of f along d at the point idx: o = 0 gives the
+ * forward derivative (D+, result at c+1/2 from f at integer points), o = -1
+ * the backward one (D-, result at c from f at half points j+1/2 stored at j).
+ * Taylor weights, or the time-space stencil when the per-cell arrays are set. */
+static double stag(const orc_coeffs *g, const double *f, int i0, int i1, int i2, int d, int o)
 {
     int idx[3] = {i0, i1, i2};
     int c = idx[d];
     size_t base = ((size_t)i2 * g->n[1] + i1) * g->n[0] + i0;
     double s = 0.0;
-    for (int m = 1; m <= 4; ++m)
-        s += CM[m - 1] * (at(g, p, base, d, c, c + m) - at(g, p, base, d, c, c - m + 1));
+    for (int m = 1; m <= 4; ++m) {
+        double w = g->thb ? g->tha[m - 1][base] : CM[m - 1];
+        s += w * (at(g, f, base, d, c, c + m + o) - at(g, f, base, d, c, c - m + 1 + o));
+    }
+    if (g->thb) {
+        double x = 0.0;
+        for (int e = 0; e < g->ndim; ++e) {
+            if (e == d) continue;
+            for (int sg = -1; sg <= 1; sg += 2)
+                x += at2(g, f, idx, e, sg, d, 1 + o) - at2(g, f, idx, e, sg, d, o);
+        }
+        s += g->thb[base] * x;
+    }
     return s / g->dx;
+}
+
+/* Forward staggered derivative of p along d, at the v_d point c+1/2. */
+static double dplus(const orc_coeffs *g, const double *p, int i0, int i1, int i2, int d)
+{
+    return stag(g, p, i0, i1, i2, d, 0);
 }
 
 /* Backward staggered derivative of v_d along d, at the p point c
  * (v_d[j] sits at j+1/2). */
 static double dminus(const orc_coeffs *g, const double *v, int i0, int i1, int i2, int d)
 {
-    int idx[3] = {i0, i1, i2};
-    int c = idx[d];
-    size_t base = ((size_t)i2 * g->n[1] + i1) * g->n[0] + i0;
-    double s = 0.0;
-    for (int m = 1; m <= 4; ++m)
-        s += CM[m - 1] * (at(g, v, base, d, c, c + m - 1) - at(g, v, base, d, c, c - m));
-    return s / g->dx;
+    return stag(g, v, i0, i1, i2, d, -1);
 }
 
 /* Exposed for the derivative pin tests. */
@@ -244,8 +286,8 @@ int orc_run(const orc_coeffs *g, orc_state *s, int n_steps, int it0,
  * and source terms of the step are applied by the caller first).  dc: the
  * derivatives of every a, b with respect to the per-voxel factor s on the
  * d of the tissue mechanisms.  grad_kdt and grad_s accumulate dL/d(K dt) and
- * dL/ds per voxel.  wq, wg: scratch fields (n points each).  Returns 0, or -1
- * when the nonlinear factor is on. */
+ * dL/ds per voxel.  wq, wg: scratch fields (n points each).  Returns 0, -1
+ * when the nonlinear factor is on, or -2 with the time-space stencil. */
 typedef struct {
     const double *da1[ORC_MAXMECH][3], *db1[ORC_MAXMECH][3];   /* at v_d points */
     const double *da2[ORC_MAXMECH][3], *db2[ORC_MAXMECH][3];   /* at p points, per d */
@@ -256,6 +298,8 @@ int orc_adjoint_step(const orc_coeffs *g, const orc_state *f, double *const *vh,
                      double *const *wq, double *const *wg)
 {
     if (g->b2dt) return -1;
+    /* per-point time-space coefficients make (D+)^T differ from -D-: not covered */
+    if (g->thb) return -2;
     /* pressure half step, pointwise: adjoints of acc, psi2, and of q_d into wq */
 #pragma omp parallel for collapse(2) schedule(static)
     for (int i2 = 0; i2 < g->n[2]; ++i2)

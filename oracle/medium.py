@@ -34,6 +34,18 @@
   there, and long runs diverge (the paper's no-transition variant diverged
   in 29 cells).
 * time step from a CFL number: dt = CFL dx / max(c / sqrt(kappa_1 kappa_2)).
+* time-space stencil (Sec. 3.3: 2M-th order in space and fourth order in
+  time, after Tan & Huang, J. Comput. Phys. 276 (2014)), ``time_order=4``:
+  every first derivative along d gets, besides its on-axis differences
+  f(+m) - f(-m+1) (weights a_m), the two-point difference along d at the
+  +-1 neighbours across every other axis (weight b).  Both come from the
+  cell's Courant number r = c dt / dx by asking the plane-wave relation of
+  the leapfrog scheme, sin(omega dt / 2) = (dt / 2) c |K(k)|, to hold for
+  omega = c |k| to the orders the stencil can reach: b = r^2 / 24 from the
+  k_d k_e^2 term, and for j = 1..M
+      sum_m (2m - 1)^(2j - 1) a_m + 2 (D - 1) b = r^(2j - 2)
+  from the k_d^(2j-1) terms along the axes.  r -> 0 gives b = 0 and the
+  Taylor weights.  Velocity points use the coefficients of their cell.
 """
 from __future__ import annotations
 
@@ -67,6 +79,45 @@ def recursion_ab(d, alpha, kappa, dt):
     b = np.exp(-(d / kappa + alpha) * dt)
     a = d / (kappa * (d + kappa * alpha)) * (b - 1.0)
     return a, b
+
+
+def time_space_coefficients(r, ndim, M=4):
+    """(a [..., M], b [...]) of the time-space stencil for Courant numbers r
+    (any shape), from its plane-wave conditions (module docstring)."""
+    r = np.asarray(r, np.float64)
+    b = r * r / 24.0
+    V = np.array([[(2.0 * m - 1.0) ** (2 * j - 1) for m in range(1, M + 1)] for j in range(1, M + 1)])
+    rhs = np.stack([r ** (2 * j - 2) - 2.0 * (ndim - 1) * b for j in range(1, M + 1)], axis=-1)
+    a = np.linalg.solve(V, rhs.reshape(-1, M).T).T.reshape(r.shape + (M,))
+    return a, b
+
+
+def time_space_symbol(theta, a, b):
+    """dx/2 times the symbol magnitude of each staggered derivative for a
+    plane wave of phase advance theta[d] = k_d dx per cell: list over d of
+    sum_m a_m sin((2m-1) theta_d / 2) + b sin(theta_d / 2) sum_{e != d} 2 cos theta_e."""
+    nd = len(theta)
+    out = []
+    for d in range(nd):
+        s = sum(a[m] * np.sin((2 * m + 1) * theta[d] / 2.0) for m in range(len(a)))
+        cross = sum(2.0 * np.cos(theta[e]) for e in range(nd) if e != d)
+        out.append(s + b * np.sin(theta[d] / 2.0) * cross)
+    return out
+
+
+def time_space_cfl_limit(ndim, n_theta=65):
+    """Largest Courant number at which the lossless time-space scheme is
+    stable: r max over theta of sqrt(sum_d symbol_d^2) <= 1 (bisection over
+    r, theta on a grid over [0, pi]^D)."""
+    g = np.linspace(0.0, np.pi, n_theta)
+    th = np.meshgrid(*([g] * ndim), indexing="ij")
+    lo, hi = 0.0, 1.0
+    for _ in range(50):
+        r = 0.5 * (lo + hi)
+        a, b = time_space_coefficients(r, ndim)
+        amp = r * np.sqrt(sum(s * s for s in time_space_symbol(th, a, b)))
+        lo, hi = (r, hi) if amp.max() <= 1.0 else (lo, r)
+    return lo
 
 
 def cfl_dt(cfl, dx, c, cls, table):
@@ -148,10 +199,13 @@ class OracleMedium:
                  instead of inheriting it (the homogeneous layers compared
                  with the adaptive one in Sec. 4.6: one fixed class there);
                  c, rho and beta are inherited either way
+    time_order : 2 (leapfrog with the Taylor weights) or 4 (the time-space
+                 stencil, per-cell coefficients from r = c dt / dx)
     """
 
     def __init__(self, shape, dx, dt, c, rho, cls, params, beta=None, pml=0, transition=0,
-                 f0=3e6, R0=1e-5, periodic=None, dscale=None, tissue_ramp_on=True, layer_relax=False):
+                 f0=3e6, R0=1e-5, periodic=None, dscale=None, tissue_ramp_on=True, layer_relax=False,
+                 time_order=2):
         self.shape = tuple(shape)
         self.ndim = len(shape)
         self.dx, self.dt = float(dx), float(dt)
@@ -174,6 +228,13 @@ class OracleMedium:
         K = rho * c * c
         self.K = K
         self.kdt = K * self.dt
+        assert time_order in (2, 4)
+        self.time_order = time_order
+        self.tha = self.thb = None
+        if time_order == 4:
+            a, b = time_space_coefficients(c * self.dt / self.dx, self.ndim)
+            self.tha = [np.ascontiguousarray(a[..., m]) for m in range(4)]
+            self.thb = np.ascontiguousarray(b)
         self.b2dt = None if (beta is None or not np.any(beta)) else 2.0 * beta * self.dt
         # face density per direction (numpy axis ax <-> direction d = ndim-1-ax)
         self.dt_rho = []

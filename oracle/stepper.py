@@ -25,6 +25,7 @@ class _Coeffs(C.Structure):
         ("a1", (_P * 3) * MAXMECH), ("b1", (_P * 3) * MAXMECH),
         ("a2", (_P * 3) * MAXMECH), ("b2", (_P * 3) * MAXMECH),
         ("a1p", _P * 3), ("b1p", _P * 3), ("a2p", _P * 3), ("b2p", _P * 3),
+        ("tha", _P * 4), ("thb", _P),
     ]
 
 
@@ -130,6 +131,10 @@ class OracleSim:
             if m.a1p[d] is not None:
                 c.a1p[d], c.b1p[d] = _ptr(self._arr(m.a1p[d])), _ptr(self._arr(m.b1p[d]))
                 c.a2p[d], c.b2p[d] = _ptr(self._arr(m.a2p[d])), _ptr(self._arr(m.b2p[d]))
+        if getattr(m, "thb", None) is not None:
+            for k in range(4):
+                c.tha[k] = _ptr(self._arr(m.tha[k]))
+            c.thb = _ptr(self._arr(m.thb))
         return c
 
     def _state(self):
