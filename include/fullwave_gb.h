@@ -87,6 +87,19 @@ typedef struct fw_grid {
                         * layer, e.g. one fixed class everywhere in it (the
                         * homogeneous layers of Sec. 4.6).  c, rho and beta
                         * are inherited either way; other values: FW_ERR_ARG */
+    int time_order;    /* 2 (or 0): second-order leapfrog with the 8th-order
+                        * Taylor staggered weights.  4: the time-space stencil
+                        * of Sec. 3.3 (2M = 8th order in space, fourth order
+                        * in time, after Tan & Huang, J. Comput. Phys. 276
+                        * (2014)): every first derivative along d adds to its
+                        * on-axis differences the two-point difference along
+                        * d at the +-1 neighbours across each other axis,
+                        * with per-cell weights a_m(r), b(r) = r^2/24 from the
+                        * cell's Courant number r = c dt / dx, so that the
+                        * scheme's plane-wave relation matches omega = c |k|
+                        * to those orders.  Stability limit of c_eff dt / dx
+                        * about 0.647 (2D), 0.516 (3D), checked at creation.
+                        * Other values: FW_ERR_ARG */
 } fw_grid;
 
 /* Relaxation parameters of one class (Sec. 2.1): kappa_x1, kappa_x2 and for
@@ -130,6 +143,7 @@ typedef struct fw_medium_info {
     size_t device_bytes;
     long long step;    /* completed time steps                               */
     int n_src, n_rcv, n_rec;
+    int time_order;    /* 2 or 4 (fw_grid.time_order)                       */
 } fw_medium_info;
 
 /* ---- calibration (host, FP64) ------------------------------------------- */
@@ -212,7 +226,10 @@ int fw_create_medium(const fw_grid *g, const float *c, const float *rho, const f
  * host or device, nx*ny*nz) indexes classes[0..n_classes-1], all with the
  * same n_mech.  Per-voxel c, rho, beta as above.  A velocity point v_d[i]
  * (at i+1/2 along d) uses the class of cell i.  The stability limit on
- * c_eff*dt/dx is 1/(sqrt(D) sum|c_m|) = 0.5497 (2D), 0.4488 (3D).  Blocking. */
+ * c_eff*dt/dx is 1/(sqrt(D) sum|c_m|) = 0.5497 (2D), 0.4488 (3D) for the
+ * leapfrog; for the time-space stencil (time_order 4) creation requires
+ * (c_eff,max dt/dx) max_theta |K(theta; r)| dx/2 <= 1 for the weights of the
+ * smallest and of the largest r = c dt/dx of the map.  Blocking. */
 int fw_create_medium_classes(const fw_grid *g, const float *c, const float *rho,
                              const float *beta, const uint16_t *class_idx,
                              const fw_relax_params *classes, int n_classes, int storage,
@@ -353,8 +370,9 @@ int fw_load_state(fw_medium *m, const void *src, void *stream);
  * grad_alpha0 may be NULL.  Device memory: (ceil(n_steps/K) + K + 3) state
  * images (fw_state_bytes) plus 6 fields and 4 FP64 maps, from the installed
  * allocator, released before return.  Blocking.
- * Errors: FW_ERR_ARG, FW_ERR_UNSUPPORTED (nonlinear media, 16-bit storage, more
- * than 65535 points along either of the two slower axes),
+ * Errors: FW_ERR_ARG, FW_ERR_UNSUPPORTED (nonlinear media, 16-bit storage, the
+ * time-space stencil (time_order 4), more than 65535 points along either of
+ * the two slower axes),
  * FW_ERR_NOMEM, FW_ERR_CUDA, or the medium's sticky error. */
 int fw_gradient(fw_medium *m, int n_steps, int checkpoint_every, const void *G, const void *alpha0,
                 void *grad_c, void *grad_alpha0, int as_f64, void *stream);

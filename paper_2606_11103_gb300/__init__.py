@@ -78,10 +78,12 @@ class _Buf:
         self.ptr = C.c_void_p(arr.ctypes.data)
 
 
-def make_grid(shape, dx, dt=0.0, cfl=0.0, pml=0, transition=0, f0=3e6, pml_r0=0.0, layer_relax=False) -> fw_grid:
+def make_grid(shape, dx, dt=0.0, cfl=0.0, pml=0, transition=0, f0=3e6, pml_r0=0.0, layer_relax=False,
+              time_order=2) -> fw_grid:
     """fw_grid from a numpy-order shape (ny, nx) or (nz, ny, nx).  layer_relax:
     keep the caller's relaxation classes inside the absorbing layer instead of
-    inheriting the nearest interior class."""
+    inheriting the nearest interior class.  time_order: 2 (leapfrog) or 4
+    (the time-space stencil)."""
     g = fw_grid()
     g.ndim = len(shape)
     if g.ndim == 2:
@@ -94,6 +96,7 @@ def make_grid(shape, dx, dt=0.0, cfl=0.0, pml=0, transition=0, f0=3e6, pml_r0=0.
     g.pml, g.transition = int(pml), int(transition)
     g.f0, g.pml_r0 = float(f0), float(pml_r0)
     g.layer_relax = int(bool(layer_relax))
+    g.time_order = int(time_order)
     return g
 
 
@@ -177,8 +180,8 @@ class Medium:
     # -- construction ---------------------------------------------------------
     @classmethod
     def from_classes(cls, shape, dx, c, rho, class_idx, classes, dt=0.0, cfl=0.0, beta=None, pml=0,
-                     transition=0, f0=3e6, storage="f32", stream=None, layer_relax=False):
-        g = make_grid(shape, dx, dt, cfl, pml, transition, f0, layer_relax=layer_relax)
+                     transition=0, f0=3e6, storage="f32", stream=None, layer_relax=False, time_order=2):
+        g = make_grid(shape, dx, dt, cfl, pml, transition, f0, layer_relax=layer_relax, time_order=time_order)
         arr = (fw_relax_params * len(classes))(*classes)
         bc, br = _Buf(c, np.float32), _Buf(rho, np.float32)
         bb = _Buf(beta, np.float32) if beta is not None else None
@@ -191,8 +194,8 @@ class Medium:
 
     @classmethod
     def from_maps(cls, shape, dx, c, rho, alpha0, y, n_mech=2, dt=0.0, cfl=0.0, beta=None, pml=0,
-                  transition=0, f0=3e6, storage="f32", stream=None, layer_relax=False, **fit_kw):
-        g = make_grid(shape, dx, dt, cfl, pml, transition, f0, layer_relax=layer_relax)
+                  transition=0, f0=3e6, storage="f32", stream=None, layer_relax=False, time_order=2, **fit_kw):
+        g = make_grid(shape, dx, dt, cfl, pml, transition, f0, layer_relax=layer_relax, time_order=time_order)
         o = fit_opts(**fit_kw)
         if "c0" not in fit_kw:
             o.c0 = 0.0           # per-class mean sound speed
@@ -319,11 +322,11 @@ class Server:
 
     def submit(self, shape, dx, dt, c, rho, class_idx, classes, n_steps, src_mask=None, waves=None, wave_of=None,
                rcv_mask=None, decim=1, beta=None, pml=0, transition=0, f0=3e6, storage="f32", traces_out=None,
-               tag=0):
+               tag=0, time_order=2):
         """Queue one request; returns (id, traces_out).  traces_out (numpy or
         torch, float32 [n_rcv, n_rec]) is filled at completion."""
         r = _lib.fw_request()
-        r.grid = make_grid(shape, dx, dt, 0.0, pml, transition, f0)
+        r.grid = make_grid(shape, dx, dt, 0.0, pml, transition, f0, time_order=time_order)
         keep = [_Buf(c, np.float32), _Buf(rho, np.float32), _Buf(class_idx, np.uint16)]
         r.c, r.rho, r.class_idx = keep[0].ptr, keep[1].ptr, keep[2].ptr
         if beta is not None:

@@ -30,7 +30,7 @@ class fw_grid(C.Structure):
     _fields_ = [("ndim", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
                 ("dx", C.c_double), ("dt", C.c_double), ("cfl", C.c_double),
                 ("pml", C.c_int), ("transition", C.c_int), ("f0", C.c_double), ("pml_r0", C.c_double),
-                ("layer_relax", C.c_int)]
+                ("layer_relax", C.c_int), ("time_order", C.c_int)]
 
 
 class fw_relax_params(C.Structure):
@@ -55,7 +55,7 @@ class fw_medium_info(C.Structure):
                 ("storage", C.c_int), ("n_classes", C.c_int), ("nonlinear", C.c_int),
                 ("dx", C.c_double), ("dt", C.c_double), ("c_max", C.c_double), ("ceff_max", C.c_double),
                 ("device_bytes", C.c_size_t), ("step", C.c_longlong),
-                ("n_src", C.c_int), ("n_rcv", C.c_int), ("n_rec", C.c_int)]
+                ("n_src", C.c_int), ("n_rcv", C.c_int), ("n_rec", C.c_int), ("time_order", C.c_int)]
 
 
 class fw_server_opts(C.Structure):

@@ -542,6 +542,7 @@ extern "C" int fw_gradient(fw_medium *m, int n_steps, int checkpoint_every, cons
     if (!m || n_steps < 1 || (m->n_rcv > 0 && !G)) return FW_ERR_ARG;
     if (m->sticky) return m->sticky;
     if (m->nonlinear) return FW_ERR_UNSUPPORTED;
+    if (m->time_order == 4) return FW_ERR_UNSUPPORTED;   // the transpose of the per-cell time-space weights is not built
     if (m->storage != FW_STORE_F32 && m->storage != FW_STORE_F64) return FW_ERR_UNSUPPORTED;
     if (m->NY > 65535 || m->NZ > 65535) return FW_ERR_UNSUPPORTED;   // launch grid's y and z limits
     int K = checkpoint_every > 0 ? checkpoint_every : std::max(1, (int)std::lround(std::sqrt((double)n_steps)));

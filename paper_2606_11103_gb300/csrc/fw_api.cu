@@ -102,6 +102,77 @@ double stencil_abs_sum()
     return 1225.0 / 1024.0 + 245.0 / 3072.0 + 49.0 / 5120.0 + 5.0 / 7168.0;
 }
 
+// ---- time-space stencil (Sec. 3.3, after Tan & Huang 2014) -----------------
+// Weights of the first derivative along d: a_m on the on-axis differences
+// f(+m) - f(-m+1), b on the two-point differences at the -+1 neighbours across
+// each of the other D-1 axes.  With r = c dt/dx, b = r^2/24 and the a_m solve
+//     sum_m (2m-1)^(2j-1) a_m = r^(2j-2) - 2 (D-1) b,   j = 1..4,
+// the conditions under which the leapfrog's plane-wave relation matches
+// omega = c|k| along the axes to order k^7 and across them at k_d k_e^2.
+// The right side is a polynomial in r^2, so is every a_m:
+// a_m = sum_n ts[m][n] r^(2n); ts is found by solving the 4x4 system for the
+// four coefficient vectors of that polynomial.
+void time_space_polynomials(int ndim, double ts[4][4])
+{
+    double rhs[4][4] = {};          // rhs[n][j]: coefficient of r^(2n) in row j
+    for (int j = 0; j < 4; ++j) {
+        rhs[0][j] = j == 0 ? 1.0 : 0.0;
+        rhs[1][j] = (j == 1 ? 1.0 : 0.0) - 2.0 * (ndim - 1) / 24.0;
+        rhs[2][j] = j == 2 ? 1.0 : 0.0;
+        rhs[3][j] = j == 3 ? 1.0 : 0.0;
+    }
+    for (int n = 0; n < 4; ++n) {
+        double A[4][5];
+        for (int j = 0; j < 4; ++j) {
+            for (int mm = 0; mm < 4; ++mm) A[j][mm] = std::pow(2.0 * mm + 1.0, 2 * j + 1);
+            A[j][4] = rhs[n][j];
+        }
+        for (int col = 0; col < 4; ++col) {        // Gauss-Jordan with partial pivoting
+            int piv = col;
+            for (int r = col + 1; r < 4; ++r)
+                if (std::fabs(A[r][col]) > std::fabs(A[piv][col])) piv = r;
+            for (int c = 0; c < 5; ++c) std::swap(A[col][c], A[piv][c]);
+            for (int r = 0; r < 4; ++r) {
+                if (r == col) continue;
+                const double f = A[r][col] / A[col][col];
+                for (int c = col; c < 5; ++c) A[r][c] -= f * A[col][c];
+            }
+        }
+        for (int mm = 0; mm < 4; ++mm) ts[mm][n] = A[mm][4] / A[mm][mm];
+    }
+}
+
+// Largest |amplification| factor r_eff * |K(theta)| dx/2 of the lossless
+// time-space scheme over a grid of phase advances theta in [0, pi]^D, for the
+// weights of Courant number r (the scheme is stable where it is <= 1).
+double time_space_amplification(int ndim, const double ts[4][4], double r, double r_eff)
+{
+    const double kPi = 3.14159265358979323846;
+    const double r2 = r * r, b = r2 / 24.0;
+    double a[4];
+    for (int mm = 0; mm < 4; ++mm) a[mm] = ((ts[mm][3] * r2 + ts[mm][2]) * r2 + ts[mm][1]) * r2 + ts[mm][0];
+    const int nt = 33;
+    double worst = 0.0;
+    const int n2 = ndim == 3 ? nt : 1;
+    for (int i = 0; i < nt; ++i)
+        for (int j = 0; j < nt; ++j)
+            for (int l = 0; l < n2; ++l) {
+                const double th[3] = {kPi * i / (nt - 1), kPi * j / (nt - 1), ndim == 3 ? kPi * l / (nt - 1) : 0.0};
+                double ss = 0.0;
+                for (int d = 0; d < ndim; ++d) {
+                    double s = 0.0;
+                    for (int mm = 0; mm < 4; ++mm) s += a[mm] * std::sin((2 * mm + 1) * th[d] / 2.0);
+                    double cr = 0.0;
+                    for (int e = 0; e < ndim; ++e)
+                        if (e != d) cr += 2.0 * std::cos(th[e]);
+                    s += b * std::sin(th[d] / 2.0) * cr;
+                    ss += s * s;
+                }
+                worst = std::max(worst, r_eff * std::sqrt(ss));
+            }
+    return worst;
+}
+
 // ---- device helpers for construction ---------------------------------------
 
 // Gather an unpadded user map [NZ][NY][NX] (float) into the padded layout,
@@ -282,6 +353,7 @@ int make_dims(const fw_grid *g, int n_mech, int storage, bool nl, Dims *d)
     if (g->ndim == 2 && g->nz != 1) return FW_ERR_ARG;
     if (g->pml < 0 || g->transition < 0 || (g->transition > 0 && g->pml == 0)) return FW_ERR_ARG;
     if (g->layer_relax != 0 && g->layer_relax != 1) return FW_ERR_ARG;
+    if (g->time_order != 0 && g->time_order != 2 && g->time_order != 4) return FW_ERR_ARG;
     d->ndim = g->ndim;
     d->NX = g->nx;
     d->NY = g->ndim == 3 ? g->ny : 1;
@@ -567,11 +639,13 @@ int create_common(const fw_grid *g, const float *c, const float *rho, const floa
     int rc = make_dims(g, nm, storage, beta != nullptr, &d);
     if (rc) return rc;
     const size_t n = (size_t)d.NX * d.NY * d.NZ;
+    double c_min = 0.0;
     // argument checks on the host copies
     {
         std::vector<float> hc, hr;
         if ((rc = fetch_host(c, n, hc)) || (rc = fetch_host(rho, n, hr))) return rc;
         if (check_map_positive(hc.data(), n) || check_map_positive(hr.data(), n)) return FW_ERR_ARG;
+        c_min = *std::min_element(hc.begin(), hc.end());
         std::vector<uint16_t> hk(n);
         FW_CK(cudaMemcpy(hk.data(), class_idx, n * sizeof(uint16_t), cudaMemcpyDefault));
         for (size_t i = 0; i < n; ++i)
@@ -594,6 +668,8 @@ int create_common(const fw_grid *g, const float *c, const float *rho, const floa
     m->wabs = d.wabs;
     m->n_classes = (int)classes.size();
     m->classes = classes;
+    m->time_order = g->time_order == 4 ? 4 : 2;
+    if (m->time_order == 4) time_space_polynomials(d.ndim, m->ts_a);
     Layout L = make_layout(d, m->n_classes);
     m->slab = dev_alloc(L.total);
     m->slab_bytes = L.total;
@@ -651,9 +727,19 @@ int create_common(const fw_grid *g, const float *c, const float *rho, const floa
     if (g->dt > 0) m->dt = g->dt;
     else if (g->cfl > 0) m->dt = g->cfl * g->dx / m->ceff_max;
     else { release(m); return FW_ERR_ARG; }
-    {
+    if (m->time_order == 2) {
         const double limit = 1.0 / (std::sqrt((double)d.ndim) * stencil_abs_sum());
         if (m->ceff_max * m->dt / g->dx > limit * (1.0 + 1e-9)) { release(m); return FW_ERR_ARG; }
+    } else {
+        // weights of the slowest and of the fastest cell with the fastest
+        // effective speed: the amplification falls with r at its maximum
+        // (theta = pi in every direction), so the two ends bound the map
+        const double re = m->ceff_max * m->dt / g->dx;
+        for (double cc : {c_min, m->c_max})
+            if (time_space_amplification(d.ndim, m->ts_a, cc * m->dt / g->dx, re) > 1.0 + 1e-9) {
+                release(m);
+                return FW_ERR_ARG;
+            }
     }
     // K dt and 2 beta dt
     {
@@ -1214,6 +1300,7 @@ int fw_medium_get_info(fw_medium *m, fw_medium_info *info)
     info->n_src = m->n_src;
     info->n_rcv = m->n_rcv;
     info->n_rec = m->n_rec;
+    info->time_order = m->time_order;
     return FW_OK;
 }
 

@@ -86,4 +86,6 @@ struct fw_medium {
     std::map<int, fwgb::Graph> graphs;
     int zseg = 32;
     double psi_pref = 10.0;          // pressure reference [Pa] of binary16 memory variables
+    int time_order = 2;              // 2: leapfrog; 4: time-space stencil (Sec. 3.3)
+    double ts_a[4][4] = {};          // time-space weights a_m = sum_n ts_a[m][n] r^(2n)
 };

@@ -225,6 +225,11 @@ template <typename R> struct Geo {
     R c1, c2, c3, c4;    // stencil weights / dx
     R dt;
     R lr;                // length [cells] of the tissue-mechanism ramp in the layer
+    // time-space stencil (Sec. 3.3, Tan & Huang 2014): per-cell weights
+    // a_m = sum_n ta[m][n] r2^n (divided by dx) and cross weight b = r2 tb,
+    // r2 = (c dt / dx)^2 = (K dt) r2s / rho
+    R ta[4][4];
+    R tb, r2s;
 };
 
 // Tissue mechanisms in the absorbing layer (two-stage layer, Sec. 4.6 /
@@ -256,6 +261,7 @@ template <typename R, typename SS, typename SP> struct VelArgs {
     const uint16_t *cls;
     const R *lut;
     const R *pd[3], *pa[3];      // absorbing profile at half points per axis
+    const SS *kdt;               // K dt per voxel (time-space stencil only)
 };
 
 template <typename R, typename SS, typename SP> struct PresArgs {
@@ -270,6 +276,7 @@ template <typename R, typename SS, typename SP> struct PresArgs {
     const R *lut;
     const R *pd[3], *pa[3];      // absorbing profile at integer points per axis
     Monitor *mon;
+    const SS *rho;               // density per voxel (time-space stencil only)
 };
 
 template <typename SS, typename R>
@@ -288,7 +295,7 @@ __device__ __forceinline__ void ld4_or_zero(const SS *base, bool ok, R (&v)[4])
 // [BY][4*BX] in the storage type; the derivative tiles (with halos) are
 // double-buffered by plane parity as well.
 
-template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY> struct VelSmem {
+template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY, bool TS = false> struct VelSmem {
     static constexpr int TW = 4 * BX, SW = TW + 8, SH = DIM == 3 ? BY + 7 : BY, RO = DIM == 3 ? 3 : 0;
     static constexpr int NAX = DIM == 3 ? 3 : 2;
     static constexpr size_t TILE = (size_t)BY * TW;
@@ -299,14 +306,15 @@ template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY>
     static constexpr size_t o_rn = o_pn + TILE * sizeof(SS);
     static constexpr size_t o_cls = o_rn + TILE * sizeof(SS);
     static constexpr size_t o_pml = o_cls + (TILE * 2 + 15) / 16 * 16;     // absorbing-layer psi per axis
-    static constexpr size_t stage = (o_pml + 3 * TILE * sizeof(SS) + 127) / 128 * 128;
+    static constexpr size_t o_kv = o_pml + 3 * TILE * sizeof(SS);          // K dt of plane k (time-space only)
+    static constexpr size_t stage = (o_kv + (TS ? TILE * sizeof(SS) : 0) + 127) / 128 * 128;
     // derivative tiles
     static constexpr size_t o_sp = 2 * stage;
     static constexpr size_t o_sr = o_sp + 2 * (size_t)SH * SW * sizeof(R);
     static constexpr size_t bytes = o_sr + 2 * (size_t)(BY + 1) * (TW + 4) * sizeof(R);
 };
 
-template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY> struct PresSmem {
+template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY, bool TS = false> struct PresSmem {
     static constexpr int TW = 4 * BX, SWX = TW + 8, SHY = DIM == 3 ? BY + 7 : 1;
     static constexpr size_t TILE = (size_t)BY * TW;
     static constexpr size_t o_qn = 0;
@@ -316,7 +324,8 @@ template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY>
     static constexpr size_t o_psi = o_bd + TILE * sizeof(SS);
     static constexpr size_t o_cls = o_psi + (size_t)NM * TILE * sizeof(SP);
     static constexpr size_t o_pml = o_cls + (TILE * 2 + 15) / 16 * 16;
-    static constexpr size_t stage = (o_pml + 3 * TILE * sizeof(SS) + 127) / 128 * 128;
+    static constexpr size_t o_rh = o_pml + 3 * TILE * sizeof(SS);          // rho of plane k (time-space only)
+    static constexpr size_t stage = (o_rh + (TS ? TILE * sizeof(SS) : 0) + 127) / 128 * 128;
     static constexpr size_t o_svx = 2 * stage;
     static constexpr size_t o_svy = o_svx + 2 * (size_t)BY * SWX * sizeof(R);
     static constexpr size_t bytes = o_svy + 2 * (size_t)SHY * TW * sizeof(R);
@@ -325,11 +334,11 @@ template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY>
 // ---------------------------------------------------------------------------
 // velocity sweep
 
-template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY>
+template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY, bool TS>
 __device__ __forceinline__ void vel_issue(const VelArgs<R, SS, SP> &A, unsigned char *sm, int k, int x0, int y,
                                           int xb, int yb, long long row, bool hd)
 {
-    using L = VelSmem<R, SS, SP, DIM, NM, BX, BY>;
+    using L = VelSmem<R, SS, SP, DIM, NM, BX, BY, TS>;
     const Geo<R> &G = A.g;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const long long pk = (long long)k * G.plane;
@@ -351,6 +360,7 @@ __device__ __forceinline__ void vel_issue(const VelArgs<R, SS, SP> &A, unsigned 
         const bool okr = hd && k + 1 < G.nz;
         cp_async4(reinterpret_cast<SS *>(st + L::o_rn) + e0, okr ? A.rho + pk + G.plane + row : gz, okr);
         cp_async<8>(reinterpret_cast<uint16_t *>(st + L::o_cls) + e0, hd ? (const void *)(A.cls + pk + row) : (const void *)gz, hd);
+        if (TS) cp_async4(reinterpret_cast<SS *>(st + L::o_kv) + e0, hd ? A.kdt + pk + row : gz, hd);
     }
     if (G.wabs > 0 && hd) {                   // absorbing-layer memory where this thread needs it
         const bool in[3] = {x0 < G.wabs || x0 + 3 >= G.nx - G.wabs, DIM == 3 && (y < G.wabs || y >= G.ny - G.wabs),
@@ -386,15 +396,127 @@ __device__ __forceinline__ void vel_issue(const VelArgs<R, SS, SP> &A, unsigned 
         const bool ok = yb + BY < G.ny && x0 < G.px;
         cp_async4(reinterpret_cast<SS *>(sr + BY * (L::TW + 4) + 4 * tx), ok ? A.rho + pk + (long long)(yb + BY) * G.px + x0 : gz, ok);
     }
+    // time-space stencil: the x halos of the nearest halo row on either side
+    // of the tile (the cross terms reach the corner cells of rows y -+ 1)
+    if (TS && DIM == 3 && ty < 2 && (tx == 0 || tx == BX - 1)) {
+        const int yy = ty == 0 ? yb - 1 : yb + BY;
+        const int hrow = ty == 0 ? L::RO - 1 : L::RO + BY;
+        const int xc = tx == 0 ? x0 - 4 : x0 + 4;
+        const bool ok = yy >= 0 && yy < G.ny && xc >= 0 && xc < G.px;
+        cp_async4(reinterpret_cast<SS *>(sp + hrow * L::SW + (tx == 0 ? 0 : L::TW + 4)),
+                  ok ? A.p + pk + (long long)yy * G.px + xc : gz, ok);
+    }
+}
+
+// scalar / 4-vector read-only loads of a field that the running sweep does
+// not write, zero outside the grid (ok false)
+template <typename SS, typename R>
+__device__ __forceinline__ R ldz1(const SS *p, bool ok)
+{
+    return ok ? R(__ldg(p)) : R(0);
+}
+
+// Courant-number dependent weights of the time-space stencil for one cell:
+// a[m] = sum_n ta[m][n] r2^n (Horner), b = r2 tb
+template <typename R>
+__device__ __forceinline__ void ts_weights(const Geo<R> &G, R r2, R (&a)[4], R &b)
+{
+#pragma unroll
+    for (int m = 0; m < 4; ++m) a[m] = ((G.ta[m][3] * r2 + G.ta[m][2]) * r2 + G.ta[m][1]) * r2 + G.ta[m][0];
+    b = r2 * G.tb;
+}
+
+// Gradient of p at the three faces of this thread's four cells with the
+// time-space stencil (Sec. 3.3, after Tan & Huang 2014): per cell the
+// on-axis weights a_m(r) and the cross weight b(r), r^2 = (K dt) dt /
+// (rho dx^2); the cross term along d is the sum, over the other axes e and
+// s = -+1, of the two-point difference along d at the neighbour s along e.
+// Plane k (with x/y halos and the corners of rows y -+ 1) comes from the
+// tile sp, the own columns of planes k -+ 1 from the register queue q, and
+// the few values of planes k -+ 1 off this thread's columns from the
+// read-only cache (p is not written by this sweep).
+template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY>
+__device__ __forceinline__ void vel_gradient_ts(const VelArgs<R, SS, SP> &A, const unsigned char *st, const R *sp0,
+                                                const R (&q)[8][4], const R (&rho)[4], int k, int x0, int y,
+                                                int e0, R (&g)[3][4])
+{
+    using L = VelSmem<R, SS, SP, DIM, NM, BX, BY, true>;
+    constexpr int SW = L::SW, RO = L::RO;
+    const Geo<R> &G = A.g;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    R kd[4];
+    Sm<SS>::ld(reinterpret_cast<const SS *>(st + L::o_kv) + e0, kd);
+    // row y of plane k, columns x0-4 .. x0+7
+    R w[12];
+    {
+        const R *s = sp0 + (RO + ty) * SW + 4 * tx;
+#pragma unroll
+        for (int i = 0; i < 12; ++i) w[i] = s[i];
+    }
+    const long long rowk = (long long)y * G.px;
+    const bool okm = k >= 1, okp = k + 1 < G.nz;
+    // column x0+4 of planes k-1, k+1 and column x0-1 of plane k+1 (row y)
+    const R pm4 = ldz1<SS, R>(A.p + (long long)(k - 1) * G.plane + rowk + x0 + 4, okm && x0 + 4 < G.px);
+    const R pp4 = ldz1<SS, R>(A.p + (long long)(k + 1) * G.plane + rowk + x0 + 4, okp && x0 + 4 < G.px);
+    const R ppm1 = ldz1<SS, R>(A.p + (long long)(k + 1) * G.plane + rowk + x0 - 1, okp && x0 >= 1);
+    R X[3][4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const R qm1 = e < 3 ? q[2][e + 1] : pm4, qp1 = e < 3 ? q[4][e + 1] : pp4;
+        const R pl = e > 0 ? q[4][e - 1] : ppm1;          // plane k+1, column x-1
+        X[0][e] = (qm1 - q[2][e]) + (qp1 - q[4][e]);
+        X[2][e] = (pl - w[e + 3]) + (qp1 - w[e + 5]);
+        X[1][e] = R(0);
+    }
+    if (DIM == 3) {
+        R um[5], up[6];                                   // rows y-1 (x0..x0+4), y+1 (x0-1..x0+4) of plane k
+        {
+            const R *s = sp0 + (RO + ty - 1) * SW + 4 + 4 * tx;
+#pragma unroll
+            for (int i = 0; i < 5; ++i) um[i] = s[i];
+            const R *t = sp0 + (RO + ty + 1) * SW + 3 + 4 * tx;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) up[i] = t[i];
+        }
+        R a1m[4], a1p[4], am1p[4];                        // rows y+1 of planes k-1, k+1; row y-1 of plane k+1
+        const bool oy1 = y + 1 < G.ny, oym = y >= 1;
+        ld4_or_zero(A.p + (long long)(k - 1) * G.plane + rowk + G.px + x0, okm && oy1, a1m);
+        ld4_or_zero(A.p + (long long)(k + 1) * G.plane + rowk + G.px + x0, okp && oy1, a1p);
+        ld4_or_zero(A.p + (long long)(k + 1) * G.plane + rowk - G.px + x0, okp && oym, am1p);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            X[0][e] += (um[e + 1] - um[e]) + (up[e + 2] - up[e + 1]);
+            X[1][e] = (up[e] - w[e + 3]) + (up[e + 2] - w[e + 5]) + (a1m[e] - q[2][e]) + (a1p[e] - q[4][e]);
+            X[2][e] += (am1p[e] - um[e]) + (a1p[e] - up[e + 1]);
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const bool live = x0 + e < G.nx;
+        const R r2 = live ? kd[e] * G.r2s * fw_rcp(rho[e]) : R(0);
+        R a[4], b;
+        ts_weights(G, r2, a, b);
+        g[0][e] = a[0] * (w[e + 5] - w[e + 4]) + a[1] * (w[e + 6] - w[e + 3]) + a[2] * (w[e + 7] - w[e + 2]) +
+                  a[3] * (w[e + 8] - w[e + 1]) + b * X[0][e];
+        if (DIM == 3) {
+            const R *c = sp0 + 4 + 4 * tx + e;
+            g[1][e] = a[0] * (c[(RO + ty + 1) * SW] - c[(RO + ty) * SW]) +
+                      a[1] * (c[(RO + ty + 2) * SW] - c[(RO + ty - 1) * SW]) +
+                      a[2] * (c[(RO + ty + 3) * SW] - c[(RO + ty - 2) * SW]) +
+                      a[3] * (c[(RO + ty + 4) * SW] - c[(RO + ty - 3) * SW]) + b * X[1][e];
+        }
+        g[2][e] = a[0] * (q[4][e] - q[3][e]) + a[1] * (q[5][e] - q[2][e]) + a[2] * (q[6][e] - q[1][e]) +
+                  a[3] * (q[7][e] - q[0][e]) + b * X[2][e];
+    }
 }
 
 // 3D: 32-bit memory variables fill shared memory at two CTAs per SM, 16-bit
 // ones fit three (registers are held to the matching share)
-template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY>
-__global__ void __launch_bounds__(BX *BY, DIM == 3 ? ((BY < 8 && sizeof(SP) == 2) ? 3 : 2) : 1)
+template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY, bool TS>
+__global__ void __launch_bounds__(BX *BY, DIM == 3 ? ((BY < 8 && sizeof(SP) == 2 && !TS) ? 3 : 2) : 1)
 k_velocity(const VelArgs<R, SS, SP> A)
 {
-    using L = VelSmem<R, SS, SP, DIM, NM, BX, BY>;
+    using L = VelSmem<R, SS, SP, DIM, NM, BX, BY, TS>;
     constexpr int TW = L::TW, SW = L::SW, SH = L::SH, RO = L::RO;
     static_assert(sizeof(SS) == sizeof(R), "state is stored in the arithmetic type");
     extern __shared__ __align__(128) unsigned char smem[];
@@ -417,7 +539,7 @@ k_velocity(const VelArgs<R, SS, SP> A)
         ld4_or_zero(A.p + kk * G.plane + row, hd && kk >= 0 && kk < G.nz, q[j]);
     }
     ld4_or_zero(A.rho + z0 * G.plane + row, hd && z0 < G.nz, rq[0]);
-    if (z0 < z1) vel_issue<R, SS, SP, DIM, NM, BX, BY>(A, smem, z0, x0, y, xb, yb, row, hd);
+    if (z0 < z1) vel_issue<R, SS, SP, DIM, NM, BX, BY, TS>(A, smem, z0, x0, y, xb, yb, row, hd);
     cp_commit();
     // absorbing-layer profile of this thread's x and y positions (fixed over the march)
     const bool pml_x = G.wabs > 0 && (x0 < G.wabs || x0 + 3 >= G.nx - G.wabs);
@@ -454,7 +576,7 @@ k_velocity(const VelArgs<R, SS, SP> A)
             R *r = &sr[ty][4 * tx];
             r[0] = rq[0][0]; r[1] = rq[0][1]; r[2] = rq[0][2]; r[3] = rq[0][3];
         }
-        if (k + 1 < z1) vel_issue<R, SS, SP, DIM, NM, BX, BY>(A, smem, k + 1, x0, y, xb, yb, row, hd);
+        if (k + 1 < z1) vel_issue<R, SS, SP, DIM, NM, BX, BY, TS>(A, smem, k + 1, x0, y, xb, yb, row, hd);
         cp_commit();
         const bool pml_z = G.wabs > 0 && (k < G.wabs || k >= G.nz - G.wabs);
         R pdz = 0, paz = 0;
@@ -465,6 +587,9 @@ k_velocity(const VelArgs<R, SS, SP> A)
         Sm<SS>::ld(reinterpret_cast<const SS *>(st + L::o_rn) + e0, rq[1]);
         if (hd) {
             R g[3][4];
+            if (TS) {
+                vel_gradient_ts<R, SS, SP, DIM, NM, BX, BY>(A, st, &sp[0][0], q, rq[0], k, x0, y, e0, g);
+            } else {
             {
                 R w[12];
                 const R *s = &sp[RO + ty][4 * tx];
@@ -491,6 +616,7 @@ k_velocity(const VelArgs<R, SS, SP> A)
             for (int e = 0; e < 4; ++e)
                 g[2][e] = G.c1 * (q[4][e] - q[3][e]) + G.c2 * (q[5][e] - q[2][e]) +
                           G.c3 * (q[6][e] - q[1][e]) + G.c4 * (q[7][e] - q[0][e]);
+            }
             R dtr[3][4];
             {
                 const R *r0 = &sr[ty][4 * tx];
@@ -595,11 +721,11 @@ k_velocity(const VelArgs<R, SS, SP> A)
 // ---------------------------------------------------------------------------
 // pressure sweep
 
-template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY, bool NL>
+template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY, bool NL, bool TS>
 __device__ __forceinline__ void pres_issue(const PresArgs<R, SS, SP> &A, unsigned char *sm, int k, int x0, int y,
                                            int yb, long long row, bool hd)
 {
-    using L = PresSmem<R, SS, SP, DIM, NM, BX, BY>;
+    using L = PresSmem<R, SS, SP, DIM, NM, BX, BY, TS>;
     const Geo<R> &G = A.g;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const long long pk = (long long)k * G.plane;
@@ -613,6 +739,7 @@ __device__ __forceinline__ void pres_issue(const PresArgs<R, SS, SP> &A, unsigne
     cp_async4(reinterpret_cast<SS *>(st + L::o_p) + e0, hd ? A.p + pk + row : gz, hd);
     cp_async4(reinterpret_cast<SS *>(st + L::o_kd) + e0, hd ? A.kdt + pk + row : gz, hd);
     if (NL) cp_async4(reinterpret_cast<SS *>(st + L::o_bd) + e0, hd ? A.b2dt + pk + row : gz, hd);
+    if (TS) cp_async4(reinterpret_cast<SS *>(st + L::o_rh) + e0, hd ? A.rho + pk + row : gz, hd);
 #pragma unroll
     for (int m = 0; m < NM; ++m)
         cp_async4(reinterpret_cast<SP *>(st + L::o_psi) + m * L::TILE + e0,
@@ -648,11 +775,122 @@ __device__ __forceinline__ void pres_issue(const PresArgs<R, SS, SP> &A, unsigne
     }
 }
 
-template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY, bool NL>
-__global__ void __launch_bounds__(BX *BY, DIM == 3 ? (BY < 8 ? 3 : 2) : 1)
+// Divergence terms q_d = D-_d v_d at this thread's four cells with the
+// time-space stencil (Sec. 3.3, after Tan & Huang 2014), the counterpart of
+// vel_gradient_ts: per-cell weights from r^2 = (K dt) dt / (rho dx^2); the
+// cross term along d sums, over the other axes e and s = -+1, the two-point
+// difference v_d(i) - v_d(i-1) along d at the neighbour s along e.  v_x of
+// plane k comes from the tile svx (x halo), v_y from svy (y halo), v_z from
+// the register queue; the values of the neighbour rows and planes from the
+// read-only cache (v is not written by this sweep).
+template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY>
+__device__ __forceinline__ void pres_divergence_ts(const PresArgs<R, SS, SP> &A, const unsigned char *st,
+                                                   const R *svx0, const R *svy0, const R (&qz)[8][4],
+                                                   const R (&kd)[4], int k, int x0, int y, int e0, R (&qd)[3][4])
+{
+    using L = PresSmem<R, SS, SP, DIM, NM, BX, BY, true>;
+    constexpr int TW = L::TW, SWX = L::SWX;
+    const Geo<R> &G = A.g;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    R rh[4];
+    Sm<SS>::ld(reinterpret_cast<const SS *>(st + L::o_rh) + e0, rh);
+    const long long rowk = (long long)y * G.px;
+    const bool okm = k >= 1, okp = k + 1 < G.nz, oxl = x0 >= 1;
+    // five values x0-1 .. x0+3 of field f in row rr of plane kk
+    auto five = [&](const SS *f, int kk, long long rr, bool ok, R (&o)[5]) {
+        R t[4];
+        ld4_or_zero(f + (long long)kk * G.plane + rr + x0, ok, t);
+        o[0] = ldz1<SS, R>(f + (long long)kk * G.plane + rr + x0 - 1, ok && oxl);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) o[i + 1] = t[i];
+    };
+    R w[12];
+    {
+        const R *s = svx0 + ty * SWX + 4 * tx;
+#pragma unroll
+        for (int i = 0; i < 12; ++i) w[i] = s[i];
+    }
+    R X[3][4];
+    {   // v_x: planes k -+ 1 of row y; rows y -+ 1 of plane k (3D)
+        R m[5], p[5];
+        five(A.v[0], k - 1, rowk, okm, m);
+        five(A.v[0], k + 1, rowk, okp, p);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) X[0][e] = (m[e + 1] - m[e]) + (p[e + 1] - p[e]);
+        if (DIM == 3) {
+            five(A.v[0], k, rowk - G.px, y >= 1, m);
+            five(A.v[0], k, rowk + G.px, y + 1 < G.ny, p);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) X[0][e] += (m[e + 1] - m[e]) + (p[e + 1] - p[e]);
+        }
+    }
+    {   // v_z: columns x -+ 1 of planes k, k-1 (own columns from the queue); rows y -+ 1 (3D)
+        const R l0 = ldz1<SS, R>(A.v[2] + (long long)k * G.plane + rowk + x0 - 1, oxl);
+        const R l1 = ldz1<SS, R>(A.v[2] + (long long)(k - 1) * G.plane + rowk + x0 - 1, oxl && okm);
+        const R r0 = ldz1<SS, R>(A.v[2] + (long long)k * G.plane + rowk + x0 + 4, x0 + 4 < G.px);
+        const R r1 = ldz1<SS, R>(A.v[2] + (long long)(k - 1) * G.plane + rowk + x0 + 4, x0 + 4 < G.px && okm);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const R a0 = e > 0 ? qz[4][e - 1] : l0, a1 = e > 0 ? qz[3][e - 1] : l1;
+            const R b0 = e < 3 ? qz[4][e + 1] : r0, b1 = e < 3 ? qz[3][e + 1] : r1;
+            X[2][e] = (a0 - a1) + (b0 - b1);
+        }
+        if (DIM == 3) {
+            R m0[4], m1[4], p0[4], p1[4];
+            ld4_or_zero(A.v[2] + (long long)k * G.plane + rowk - G.px + x0, y >= 1, m0);
+            ld4_or_zero(A.v[2] + (long long)(k - 1) * G.plane + rowk - G.px + x0, y >= 1 && okm, m1);
+            ld4_or_zero(A.v[2] + (long long)k * G.plane + rowk + G.px + x0, y + 1 < G.ny, p0);
+            ld4_or_zero(A.v[2] + (long long)(k - 1) * G.plane + rowk + G.px + x0, y + 1 < G.ny && okm, p1);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) X[2][e] += (m0[e] - m1[e]) + (p0[e] - p1[e]);
+        }
+    }
+    if (DIM == 3) {   // v_y: columns x -+ 1 of rows y, y-1 (tile svy, ends from the cache); planes k -+ 1
+        const R *c0 = svy0 + (4 + ty) * TW, *c1 = svy0 + (3 + ty) * TW;
+        const R l0 = tx > 0 ? c0[4 * tx - 1] : ldz1<SS, R>(A.v[1] + (long long)k * G.plane + rowk + x0 - 1, oxl);
+        const R l1 = tx > 0 ? c1[4 * tx - 1]
+                            : ldz1<SS, R>(A.v[1] + (long long)k * G.plane + rowk - G.px + x0 - 1, oxl && y >= 1);
+        const R r0 = tx < BX - 1 ? c0[4 * tx + 4]
+                                 : ldz1<SS, R>(A.v[1] + (long long)k * G.plane + rowk + x0 + 4, x0 + 4 < G.px);
+        const R r1 = tx < BX - 1 ? c1[4 * tx + 4]
+                                 : ldz1<SS, R>(A.v[1] + (long long)k * G.plane + rowk - G.px + x0 + 4,
+                                               x0 + 4 < G.px && y >= 1);
+        R m0[4], m1[4], p0[4], p1[4];
+        ld4_or_zero(A.v[1] + (long long)(k - 1) * G.plane + rowk + x0, okm, m0);
+        ld4_or_zero(A.v[1] + (long long)(k - 1) * G.plane + rowk - G.px + x0, okm && y >= 1, m1);
+        ld4_or_zero(A.v[1] + (long long)(k + 1) * G.plane + rowk + x0, okp, p0);
+        ld4_or_zero(A.v[1] + (long long)(k + 1) * G.plane + rowk - G.px + x0, okp && y >= 1, p1);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const R a0 = e > 0 ? c0[4 * tx + e - 1] : l0, a1 = e > 0 ? c1[4 * tx + e - 1] : l1;
+            const R b0 = e < 3 ? c0[4 * tx + e + 1] : r0, b1 = e < 3 ? c1[4 * tx + e + 1] : r1;
+            X[1][e] = (a0 - a1) + (b0 - b1) + (m0[e] - m1[e]) + (p0[e] - p1[e]);
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const bool live = x0 + e < G.nx;
+        const R r2 = live ? kd[e] * G.r2s * fw_rcp(rh[e]) : R(0);
+        R a[4], b;
+        ts_weights(G, r2, a, b);
+        qd[0][e] = a[0] * (w[e + 4] - w[e + 3]) + a[1] * (w[e + 5] - w[e + 2]) + a[2] * (w[e + 6] - w[e + 1]) +
+                   a[3] * (w[e + 7] - w[e + 0]) + b * X[0][e];
+        if (DIM == 3) {
+            const R *c = svy0 + 4 * tx + e;
+            qd[1][e] = a[0] * (c[(4 + ty) * TW] - c[(3 + ty) * TW]) + a[1] * (c[(5 + ty) * TW] - c[(2 + ty) * TW]) +
+                       a[2] * (c[(6 + ty) * TW] - c[(1 + ty) * TW]) + a[3] * (c[(7 + ty) * TW] - c[(0 + ty) * TW]) +
+                       b * X[1][e];
+        }
+        qd[2][e] = a[0] * (qz[4][e] - qz[3][e]) + a[1] * (qz[5][e] - qz[2][e]) + a[2] * (qz[6][e] - qz[1][e]) +
+                   a[3] * (qz[7][e] - qz[0][e]) + b * X[2][e];
+    }
+}
+
+template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY, bool NL, bool TS>
+__global__ void __launch_bounds__(BX *BY, DIM == 3 ? ((BY < 8 && !TS) ? 3 : 2) : 1)
 k_pressure(const PresArgs<R, SS, SP> A)
 {
-    using L = PresSmem<R, SS, SP, DIM, NM, BX, BY>;
+    using L = PresSmem<R, SS, SP, DIM, NM, BX, BY, TS>;
     constexpr int TW = L::TW, SWX = L::SWX, SHY = L::SHY;
     extern __shared__ __align__(128) unsigned char smem[];
 
@@ -674,7 +912,7 @@ k_pressure(const PresArgs<R, SS, SP> A)
     }
     R pmax = R(0);
     bool bad = false;
-    if (z0 < z1) pres_issue<R, SS, SP, DIM, NM, BX, BY, NL>(A, smem, z0, x0, y, yb, row, hd);
+    if (z0 < z1) pres_issue<R, SS, SP, DIM, NM, BX, BY, NL, TS>(A, smem, z0, x0, y, yb, row, hd);
     cp_commit();
     const bool pml_x = G.wabs > 0 && (x0 < G.wabs || x0 + 3 >= G.nx - G.wabs);
     const bool pml_y = DIM == 3 && G.wabs > 0 && (y < G.wabs || y >= G.ny - G.wabs);
@@ -700,7 +938,7 @@ k_pressure(const PresArgs<R, SS, SP> A)
         const R(*svx)[SWX] = reinterpret_cast<const R(*)[SWX]>(smem + L::o_svx + buf * (size_t)BY * SWX * sizeof(R));
         const R(*svy)[TW] = reinterpret_cast<const R(*)[TW]>(smem + L::o_svy + buf * (size_t)SHY * TW * sizeof(R));
         __syncthreads();
-        if (k + 1 < z1) pres_issue<R, SS, SP, DIM, NM, BX, BY, NL>(A, smem, k + 1, x0, y, yb, row, hd);
+        if (k + 1 < z1) pres_issue<R, SS, SP, DIM, NM, BX, BY, NL, TS>(A, smem, k + 1, x0, y, yb, row, hd);
         cp_commit();
         const bool pml_z = G.wabs > 0 && (k < G.wabs || k >= G.nz - G.wabs);
         R pdz = 0, paz = 0;
@@ -710,6 +948,11 @@ k_pressure(const PresArgs<R, SS, SP> A)
         Sm<SS>::ld(reinterpret_cast<const SS *>(st + L::o_qn) + e0, qz[7]);
         if (hd) {
             R qd[3][4];
+            R pv[4], kd[4], bd[4], ps[NM][4];
+            Sm<SS>::ld(reinterpret_cast<const SS *>(st + L::o_kd) + e0, kd);
+            if (TS) {
+                pres_divergence_ts<R, SS, SP, DIM, NM, BX, BY>(A, st, &svx[0][0], &svy[0][0], qz, kd, k, x0, y, e0, qd);
+            } else {
             {
                 R w[12];
                 const R *s = &svx[ty][4 * tx];
@@ -736,9 +979,8 @@ k_pressure(const PresArgs<R, SS, SP> A)
             for (int e = 0; e < 4; ++e)
                 qd[2][e] = G.c1 * (qz[4][e] - qz[3][e]) + G.c2 * (qz[5][e] - qz[2][e]) +
                            G.c3 * (qz[6][e] - qz[1][e]) + G.c4 * (qz[7][e] - qz[0][e]);
-            R pv[4], kd[4], bd[4], ps[NM][4];
+            }
             Sm<SS>::ld(reinterpret_cast<const SS *>(st + L::o_p) + e0, pv);
-            Sm<SS>::ld(reinterpret_cast<const SS *>(st + L::o_kd) + e0, kd);
             if (NL) Sm<SS>::ld(reinterpret_cast<const SS *>(st + L::o_bd) + e0, bd);
 #pragma unroll
             for (int m = 0; m < NM; ++m) Sm<SP>::ld(reinterpret_cast<const SP *>(st + L::o_psi) + m * L::TILE + e0, ps[m]);

@@ -38,28 +38,32 @@ template <typename R> Geo<R> make_geo(const fw_medium *m)
     g.c4 = R(cm[3] / m->dx);
     g.dt = R(m->dt);
     g.lr = R(m->g.transition > 0 ? m->g.transition : 0.5 * m->g.pml);
+    for (int i = 0; i < 4; ++i)
+        for (int n = 0; n < 4; ++n) g.ta[i][n] = R(m->ts_a[i][n] / m->dx);
+    g.tb = R(1.0 / (24.0 * m->dx));
+    g.r2s = R(m->dt / (m->dx * m->dx));
     return g;
 }
 
 // which: bit 0 = velocity sweep, bit 1 = pressure sweep, bit 2 = only opt the
 // instances into their dynamic shared memory (done once at medium creation,
 // outside any stream capture)
-template <typename R, typename SS, typename SP, int DIM, int NM>
+template <typename R, typename SS, typename SP, int DIM, int NM, bool TS>
 cudaError_t launch_dn(const fw_medium *m, cudaStream_t s, int which)
 {
     constexpr int BX = DIM == 3 ? Tile3<R>::BX : Tile2<R>::BX;
     constexpr int BYV = DIM == 3 ? Tile3<R>::BYV : Tile2<R>::BYV;
     constexpr int BYP = DIM == 3 ? Tile3<R>::BYP : Tile2<R>::BYP;
-    using LV = VelSmem<R, SS, SP, DIM, NM, BX, BYV>;
-    using LP = PresSmem<R, SS, SP, DIM, NM, BX, BYP>;
+    using LV = VelSmem<R, SS, SP, DIM, NM, BX, BYV, TS>;
+    using LP = PresSmem<R, SS, SP, DIM, NM, BX, BYP, TS>;
     if (which & 4) {
-        cudaError_t e = cudaFuncSetAttribute(k_velocity<R, SS, SP, DIM, NM, BX, BYV>,
+        cudaError_t e = cudaFuncSetAttribute(k_velocity<R, SS, SP, DIM, NM, BX, BYV, TS>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LV::bytes);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_pressure<R, SS, SP, DIM, NM, BX, BYP, true>,
+            e = cudaFuncSetAttribute(k_pressure<R, SS, SP, DIM, NM, BX, BYP, true, TS>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LP::bytes);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_pressure<R, SS, SP, DIM, NM, BX, BYP, false>,
+            e = cudaFuncSetAttribute(k_pressure<R, SS, SP, DIM, NM, BX, BYP, false, TS>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LP::bytes);
         return e;
     }
@@ -79,8 +83,9 @@ cudaError_t launch_dn(const fw_medium *m, cudaStream_t s, int which)
     va.rho = static_cast<const SS *>(m->rho);
     va.cls = m->cls;
     va.lut = static_cast<const R *>(m->lut);
+    va.kdt = static_cast<const SS *>(m->kdt);
     if (which & 1)
-        k_velocity<R, SS, SP, DIM, NM, BX, BYV><<<dim3(gx, (m->NY + BYV - 1) / BYV, gz), dim3(BX, BYV), LV::bytes, s>>>(va);
+        k_velocity<R, SS, SP, DIM, NM, BX, BYV, TS><<<dim3(gx, (m->NY + BYV - 1) / BYV, gz), dim3(BX, BYV), LV::bytes, s>>>(va);
     if (!(which & 2)) return cudaGetLastError();
 
     PresArgs<R, SS, SP> pa{};
@@ -98,25 +103,33 @@ cudaError_t launch_dn(const fw_medium *m, cudaStream_t s, int which)
     pa.cls = m->cls;
     pa.lut = static_cast<const R *>(m->lut);
     pa.mon = m->mon;
+    pa.rho = static_cast<const SS *>(m->rho);
     const dim3 gp(gx, (m->NY + BYP - 1) / BYP, gz), bp(BX, BYP);
     if (m->nonlinear)
-        k_pressure<R, SS, SP, DIM, NM, BX, BYP, true><<<gp, bp, LP::bytes, s>>>(pa);
+        k_pressure<R, SS, SP, DIM, NM, BX, BYP, true, TS><<<gp, bp, LP::bytes, s>>>(pa);
     else
-        k_pressure<R, SS, SP, DIM, NM, BX, BYP, false><<<gp, bp, LP::bytes, s>>>(pa);
+        k_pressure<R, SS, SP, DIM, NM, BX, BYP, false, TS><<<gp, bp, LP::bytes, s>>>(pa);
     return cudaGetLastError();
 }
 
-template <typename R, typename SS, typename SP>
-cudaError_t launch_sweeps(const fw_medium *m, cudaStream_t s, int which)
+template <typename R, typename SS, typename SP, bool TS>
+cudaError_t launch_ts(const fw_medium *m, cudaStream_t s, int which)
 {
     const bool d3 = m->ndim == 3;
     switch (m->nmech) {
-    case 1: return d3 ? launch_dn<R, SS, SP, 3, 1>(m, s, which) : launch_dn<R, SS, SP, 2, 1>(m, s, which);
-    case 2: return d3 ? launch_dn<R, SS, SP, 3, 2>(m, s, which) : launch_dn<R, SS, SP, 2, 2>(m, s, which);
-    case 3: return d3 ? launch_dn<R, SS, SP, 3, 3>(m, s, which) : launch_dn<R, SS, SP, 2, 3>(m, s, which);
-    case 4: return d3 ? launch_dn<R, SS, SP, 3, 4>(m, s, which) : launch_dn<R, SS, SP, 2, 4>(m, s, which);
+    case 1: return d3 ? launch_dn<R, SS, SP, 3, 1, TS>(m, s, which) : launch_dn<R, SS, SP, 2, 1, TS>(m, s, which);
+    case 2: return d3 ? launch_dn<R, SS, SP, 3, 2, TS>(m, s, which) : launch_dn<R, SS, SP, 2, 2, TS>(m, s, which);
+    case 3: return d3 ? launch_dn<R, SS, SP, 3, 3, TS>(m, s, which) : launch_dn<R, SS, SP, 2, 3, TS>(m, s, which);
+    case 4: return d3 ? launch_dn<R, SS, SP, 3, 4, TS>(m, s, which) : launch_dn<R, SS, SP, 2, 4, TS>(m, s, which);
     default: return cudaErrorInvalidValue;
     }
+}
+
+// leapfrog instances, or those of the time-space stencil (time_order 4)
+template <typename R, typename SS, typename SP>
+cudaError_t launch_sweeps(const fw_medium *m, cudaStream_t s, int which)
+{
+    return m->time_order == 4 ? launch_ts<R, SS, SP, true>(m, s, which) : launch_ts<R, SS, SP, false>(m, s, which);
 }
 
 template <typename R, typename SS>

@@ -31,13 +31,13 @@ class Pair:
     """The same medium on the GPU (fw.Medium) and on the oracle."""
 
     def __init__(self, fw, shape, dx, dt, c, rho, cls, params, beta=None, pml=0, transition=0, f0=3e6,
-                 storage="f32"):
+                 storage="f32", time_order=2):
         self.shape = tuple(shape)
         self.gpu = fw.Medium.from_classes(shape, dx, c, rho, cls.astype(np.uint16), [to_c(p, fw) for p in params],
                                           dt=dt, beta=beta, pml=pml, transition=transition, f0=f0,
-                                          storage=storage)
+                                          storage=storage, time_order=time_order)
         med = OracleMedium(shape, dx, dt, c, rho, cls.astype(np.int64), params, beta=beta, pml=pml,
-                           transition=transition, f0=f0)
+                           transition=transition, f0=f0, time_order=time_order)
         self.orc = OracleSim(med)
 
     def sources(self, mask, waves, wave_of=None):
