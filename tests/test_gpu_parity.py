@@ -31,6 +31,7 @@ def fw():
 
 
 def _check(res, tol):
+    print(res)
     for k, v in res.items():
         assert v < tol, (k, v, res)
 
