@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--size", type=int, default=512, help="cube side (512 = the 3D Voronoi workload)")
     ap.add_argument("--e2e-steps", type=int, default=0, help="streaming end-to-end steps (0: = --steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--time-order", type=int, default=2, choices=[2, 4],
+                    help="2: leapfrog; 4: the time-space stencil (Sec. 3.3)")
+    ap.add_argument("--no-other-scheme", action="store_true",
+                    help="skip the device-time line of the other time scheme")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", default="voronoi3d", choices=["voronoi3d", "twolayer2d", "serving", "adjoint"],
                     help="serving: the mixed 2D/3D request stream through the continuous-batching server")
@@ -59,6 +63,7 @@ def parse():
     ap.add_argument("--gradients", type=int, default=3, help="adjoint: timed gradients")
     ap.add_argument("--slots", type=int, default=8, help="serving: admitted requests at once")
     ap.add_argument("--load", type=float, default=0.8, help="serving: offered load / one-at-a-time capacity")
+    ap.add_argument("--no-capacity", action="store_true", help="serving: skip the all-at-once capacity arms")
     return ap.parse_args()
 
 
@@ -140,9 +145,12 @@ def fit_classes(triples):
     return out, reps
 
 
-def alg_bytes(ndim, nmech, storage, nonlinear, wabs, shape):
+def alg_bytes(ndim, nmech, storage, nonlinear, wabs, shape, time_order=2):
     """Algorithmic bytes per voxel of each sweep and of the minimal single-pass
-    step (every field read once and written once, maps read once)."""
+    step (every field read once and written once, maps read once).  The
+    time-space stencil's per-cell weights need K dt in the velocity sweep and
+    rho in the pressure sweep (4 B each); the single-pass minimum reads both
+    maps once either way."""
     es = 4
     eps = {"f32": 4, "bf16": 2, "f16": 2}[storage]
     D = ndim
@@ -161,6 +169,9 @@ def alg_bytes(ndim, nmech, storage, nonlinear, wabs, shape):
     pres = D * es + 2 * es + 2 * nmech * eps + es + (es if nonlinear else 0) + 2 + pml_p
     single = 2 * es + 2 * D * es + 2 * D * nmech * eps + 2 * nmech * eps + es + es + 2 + \
         (es if nonlinear else 0) + pml_v + pml_p
+    if time_order == 4:
+        vel += es
+        pres += es
     return vel, pres, single
 
 
@@ -258,7 +269,7 @@ def oracle_sample(kind):
     return "%d^3 crop of the 512^3 Voronoi workload (N=4, 20-cell PML)" % crop
 
 
-def oracle_sim(kind, n_steps=8):
+def oracle_sim(kind, n_steps=8, time_order=2):
     from oracle import fit
     from oracle.medium import OracleMedium
     from oracle.stepper import OracleSim
@@ -281,15 +292,15 @@ def oracle_sim(kind, n_steps=8):
         p, _ = fit.fit_relaxation(float(a), float(y), 4, maxiter=200, w_list=(0.5,))
         params.append(p)
     med = OracleMedium(spec.shape, spec.dx, spec.dt, spec.maps["c"], spec.maps["rho"], cls, params, beta=beta,
-                       pml=spec.pml, f0=spec.f0)
+                       pml=spec.pml, f0=spec.f0, time_order=time_order)
     sim = OracleSim(med)
     sim.set_sources(spec.src_mask, spec.src_waves.astype(np.float64), spec.src_wave_of)
     sim.set_receivers(spec.rcv_mask, n_steps)
     return sim, int(np.prod(spec.shape))
 
 
-def time_oracle(budget_s, kind="voronoi3d"):
-    sim, vox = oracle_sim(kind, n_steps=4096)
+def time_oracle(budget_s, kind="voronoi3d", time_order=2):
+    sim, vox = oracle_sim(kind, n_steps=4096, time_order=time_order)
     sim.run(1)                      # thread start-up
     t0 = time.perf_counter()
     sim.run(2)
@@ -310,12 +321,14 @@ def metric_name(args):
 
 def workload_config(args, l2, parallelism):
     """The config object both arms print (the reference arm times a crop of it)."""
+    scheme = scheme_name(getattr(args, "time_order", 2))
     if args.workload == "twolayer2d":
         return {"workload": "2D two-layer 2048^2 (c 1580/1450, rho 1060/950, alpha0 1.09/0.6, y 1.0/1.5, "
                             "beta 3.5/6), N=4, 30-cell PML, 3 MHz line source",
-                "voxels": 2048 ** 2, "storage": args.storage, "l2": l2, "parallelism": parallelism}
+                "voxels": 2048 ** 2, "storage": args.storage, "scheme": scheme, "l2": l2, "parallelism": parallelism}
     return {"workload": "3D seeded Voronoi %d^3, 8 classes, N=4, 20-cell PML, focused 3 MHz aperture" % args.size,
-            "voxels": args.size ** 3, "storage": args.storage, "l2": l2, "parallelism": parallelism}
+            "voxels": args.size ** 3, "storage": args.storage, "scheme": scheme, "l2": l2,
+            "parallelism": parallelism}
 
 
 def reference_config(args):
@@ -336,7 +349,7 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    sim, vox = oracle_sim(args.workload, n_steps=args.warmup + args.steps + 1)
+    sim, vox = oracle_sim(args.workload, n_steps=args.warmup + args.steps + 1, time_order=args.time_order)
     sim.run(args.warmup)
     t0 = time.perf_counter()
     sim.run(args.steps)
@@ -389,7 +402,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
     m = fw.Medium.from_classes(spec.shape, spec.dx, spec.maps["c"], spec.maps["rho"], cls_map, classes,
-                               dt=spec.dt, beta=beta, pml=spec.pml, f0=spec.f0, storage=args.storage)
+                               dt=spec.dt, beta=beta, pml=spec.pml, f0=spec.f0, storage=args.storage,
+                               time_order=args.time_order)
     m.set_sources(spec.src_mask, spec.src_waves, spec.src_wave_of)
     m.set_receivers(spec.rcv_mask, n_total)
     t_create = time.perf_counter() - t0
@@ -446,13 +460,16 @@ def run_ours(args):
     assert np.isfinite(h_r.numpy()).all()
 
     # ---- roofline of the dominant kernel (velocity sweep) ----
-    b_vel, b_pres, b_single = alg_bytes(len(spec.shape), 4, args.storage, beta is not None, spec.pml, spec.shape)
+    b_vel, b_pres, b_single = alg_bytes(len(spec.shape), 4, args.storage, beta is not None, spec.pml, spec.shape,
+                                        args.time_order)
     peak, peak_kind = measured_peaks()
     t_vel = ms_v.value / K / 1e3
     t_pres = ms_p.value / K / 1e3
     ach = b_vel * vox / t_vel / 1e9
     tkey = "velocity" if args.storage == "f32" else "velocity_" + args.storage
-    traffic = profiled_traffic(vox, tkey + ("_2d" if args.workload == "twolayer2d" else ""))
+    tkey += "_2d" if args.workload == "twolayer2d" else ""
+    tkey += "_ts" if args.time_order == 4 else ""
+    traffic = profiled_traffic(vox, tkey)
     roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
             "frac": round(ach / peak, 4), "traffic": traffic, "kernel": "k_velocity (velocity sweep)",
             "peak_source": "%s hbm_gbs" % peak_kind}
@@ -482,8 +499,10 @@ def run_ours(args):
         "max_abs_p": pmax,
     }
     m.close()
+    if not args.no_other_scheme:
+        out["other_scheme"] = other_scheme(fw, L, args, spec, cls_map, classes, beta, n_total, stream, vox, peak)
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = time_oracle(args.cpu_seconds, args.workload)
+        out["cpu_baseline"] = time_oracle(args.cpu_seconds, args.workload, args.time_order)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -491,15 +510,50 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
 
 
+def scheme_name(order):
+    return "time-space stencil (4th order in time, Sec. 3.3)" if order == 4 else "leapfrog (2nd order in time)"
+
+
+def other_scheme(fw, L, args, spec, cls_map, classes, beta, n_total, stream, vox, peak):
+    """Device time of the same workload with the other time scheme (same
+    medium, sources and step count; CUDA events on the launch stream), for
+    the comparison of the two schemes beside the headline line."""
+    order = 6 - args.time_order
+    m = fw.Medium.from_classes(spec.shape, spec.dx, spec.maps["c"], spec.maps["rho"], cls_map, classes,
+                               dt=spec.dt, beta=beta, pml=spec.pml, f0=spec.f0, storage=args.storage,
+                               time_order=order)
+    m.set_sources(spec.src_mask, spec.src_waves, spec.src_wave_of)
+    m.set_receivers(spec.rcv_mask, n_total)
+    m.run(args.warmup)
+    ms_v, ms_p, ms_io, ms_tot = C.c_double(), C.c_double(), C.c_double(), C.c_double()
+    nl = C.c_int()
+    fw.check(L.fw_step_timed(m.h, args.steps, C.c_void_p(stream.cuda_stream), C.byref(ms_v), C.byref(ms_p),
+                             C.byref(ms_io), C.byref(ms_tot), C.byref(nl)), "fw_step_timed")
+    rc, _ = m.status()
+    m.close()
+    if rc != 0:
+        raise RuntimeError("unstable run (%s): %s" % (scheme_name(order), fw.FwError(rc)))
+    K = args.steps
+    b_vel, b_pres, b_single = alg_bytes(len(spec.shape), 4, args.storage, beta is not None, spec.pml, spec.shape,
+                                        order)
+    t_vel, t_pres = ms_v.value / K / 1e3, ms_p.value / K / 1e3
+    return {"scheme": scheme_name(order), "value": round(vox * K / (ms_tot.value / 1e3) / 1e9, 3),
+            "unit": "Gvoxel-updates/s", "ms_per_step": round(ms_tot.value / K, 4),
+            "velocity_ms": round(t_vel * 1e3, 4), "pressure_ms": round(t_pres * 1e3, 4),
+            "velocity_frac": round(b_vel * vox / t_vel / 1e9 / peak, 4),
+            "pressure_frac": round(b_pres * vox / t_pres / 1e9 / peak, 4),
+            "alg_bytes_per_voxel": {"velocity": round(b_vel, 2), "pressure": round(b_pres, 2)}}
+
+
 # ---------------------------------------------------------------------------
 # serving: continuous batching vs one request at a time
 
 
-def _serving_arm(fw, media, classes, arrivals, budget, slots, streams, chunk=32):
+def _serving_arm(fw, media, classes, arrivals, budget, slots, streams, chunk=32, policy=0):
     """Replay the arrival stream through one server; returns per-request
     completions (tag -> dict) and the server-clock origin."""
     from synthetic.serving import DT, DX, F0, PML
-    srv = fw.Server(budget, max_active=slots, chunk_steps=chunk, n_streams=streams)
+    srv = fw.Server(budget, max_active=slots, chunk_steps=chunk, n_streams=streams, policy=policy)
     t0 = srv.now()
     done, i, n = {}, 0, len(media)
     last = time.perf_counter()
@@ -589,21 +643,38 @@ def run_serving(args):
     arrivals = np.cumsum(gaps) / lam
     free, _ = torch.cuda.mem_get_info()
     budget = int(min(200e9, 0.8 * free))
+    slots = args.slots
     with ClockSampler(0) as clk:
-        batched, tb = _serving_arm(fw, media, classes, arrivals, budget, args.slots, args.slots)
-    single, ts = _serving_arm(fw, media, classes, arrivals, budget, 1, 1)
+        batched, tb = _serving_arm(fw, media, classes, arrivals, budget, slots, slots, policy=0)
+        log("serving: batched (size classes) done")
+        shared, tsh = _serving_arm(fw, media, classes, arrivals, budget, slots, slots, policy=1)
+        log("serving: batched (one priority) done")
+        single, ts = _serving_arm(fw, media, classes, arrivals, budget, 1, 1, policy=1)
+        log("serving: one at a time done")
     same = sum(int(batched[k]["status"] == 0 and np.array_equal(batched[k]["traces"], single[k]["traces"]))
                for k in batched)
-    sb, ss = _arm_summary(batched, tb, arrivals), _arm_summary(single, ts, arrivals)
-    zero = np.zeros(len(media))
-    cap_b, tcb = _serving_arm(fw, media, classes, zero, budget, args.slots, args.slots)
-    cap_s, tcs = _serving_arm(fw, media, classes, zero, budget, 1, 1)
-    cb, cs = _arm_summary(cap_b, tcb, zero), _arm_summary(cap_s, tcs, zero)
+    sb, ssh, ss = (_arm_summary(batched, tb, arrivals), _arm_summary(shared, tsh, arrivals),
+                   _arm_summary(single, ts, arrivals))
+    # latency by size class (short: voxels x steps <= the server's default bound)
+    short = {k for k, q in enumerate(media) if np.prod(q["shape"]) * q["n_steps"] <= 5e9}
+    for summ, res in ((sb, batched), (ssh, shared), (ss, single)):
+        for name, keys in (("short", short), ("long", set(res) - short)):
+            lat = [res[k]["t_done"] - res[k]["t_submit"] for k in keys if k in res]
+            if lat:
+                summ[name] = {"n": len(lat), "p50_s": round(float(np.percentile(lat, 50)), 3),
+                              "p99_s": round(float(np.percentile(lat, 99)), 3)}
+    cap = {}
+    if not args.no_capacity:
+        zero = np.zeros(len(media))
+        cap_b, tcb = _serving_arm(fw, media, classes, zero, budget, slots, slots, policy=0)
+        cap_s, tcs = _serving_arm(fw, media, classes, zero, budget, 1, 1, policy=1)
+        cap = {"batched": _arm_summary(cap_b, tcb, zero), "one_at_a_time": _arm_summary(cap_s, tcs, zero)}
     out = {
-        "metric": "serving throughput, mixed 2D/3D request stream", "value": cb["value"], "unit": "Gvoxel-updates/s",
+        "metric": "serving throughput, mixed 2D/3D request stream",
+        "value": cap["batched"]["value"] if cap else sb["value"], "unit": "Gvoxel-updates/s",
         "higher_is_better": True, "p50_s": sb["p50_s"], "p99_s": sb["p99_s"],
-        "capacity": {"batched": cb, "one_at_a_time": cs},
-        "at_offered_load": {"batched": sb, "one_at_a_time": ss},
+        "capacity": cap,
+        "at_offered_load": {"batched": sb, "batched_one_priority": ssh, "one_at_a_time": ss},
         "n_requests": len(media), "identical_results": "%d/%d" % (same, len(media)),
         "offered_load": args.load, "service_rate_gvox_s": {"2d": round(rate[2] / 1e9, 2), "3d": round(rate[3] / 1e9, 2)},
         "n_gpus": 1, "dtype": "f32", "data": "synthetic",

@@ -393,14 +393,16 @@ void fw_destroy_medium(fw_medium *m);
  * owns one device arena of opts.hbm_budget bytes and a scheduler thread.
  * Requests queue in arrival order; one is admitted as soon as a slot is free
  * and its footprint (fw_medium_bytes plus source/receiver buffers and the
- * upload staging) fits in what the arena has left (first fit in arrival
- * order; a queued request skipped FW_SERVER_MAX_SKIPS times blocks the ones
- * behind it until it fits).  Admitted media are built by a worker thread
- * from the request's maps, stay resident on the device, and advance in
- * chunks of opts.chunk_steps steps through their cached CUDA graphs
- * (fw_run), each request on a stream of a pool, at most two chunks in
+ * upload staging) fits in what the arena has left (first fit in the order of
+ * opts.policy; a queued request skipped FW_SERVER_MAX_SKIPS times blocks the
+ * ones of its class behind it until it fits).  Admitted media are built by a
+ * worker thread from the request's maps, stay resident on the device, and
+ * advance in chunks of opts.chunk_steps steps through their cached CUDA
+ * graphs (fw_run), each request on a stream of a pool, at most two chunks in
  * flight per request, so the work of all admitted requests overlaps on the
- * GPU.  A finished request's traces are copied to its traces_out, its
+ * GPU: each chunk enqueues the request's tiles (the CTAs of its sweeps) and
+ * the block scheduler serves the tiles of higher-priority streams first
+ * (opts.policy).  A finished request's traces are copied to its traces_out, its
  * medium is released into the arena, and the next request is admitted.
  * Kernels are deterministic: a request's result does not depend on what
  * else is admitted.  Times are seconds on the server's clock (fw_server_now).
@@ -415,7 +417,15 @@ typedef struct fw_server_opts {
     size_t hbm_budget;   /* device arena [bytes]; requests larger are refused (FW_ERR_NOMEM) */
     int max_active;      /* admitted requests at once (slots), >= 1                           */
     int chunk_steps;     /* time steps per scheduling quantum, >= 1 (32 = one cached graph)   */
-    int n_streams;       /* device streams the quanta are spread over, >= 1                   */
+    int n_streams;       /* device streams per priority level, >= 1                           */
+    int policy;          /* 0: size classes (default): requests with voxels x steps <=
+                          * short_work are admitted ahead of the others and run on the
+                          * highest-priority streams; long requests are admitted in
+                          * arrival order, keep two slots free for short ones (when
+                          * max_active >= 4), and the oldest running one runs at a middle
+                          * priority above the other long ones.  1: arrival order, one
+                          * priority for all.  Other values: FW_ERR_ARG                      */
+    double short_work;   /* voxel-steps bound of a short request; <= 0: 5e9                   */
 } fw_server_opts;
 
 /* One simulation request.  Every pointer must stay valid until the request

@@ -312,10 +312,11 @@ class Server:
     requests on the current device).  ``submit`` keeps the request's buffers
     alive until its completion has been polled."""
 
-    def __init__(self, hbm_budget, max_active=8, chunk_steps=32, n_streams=8):
+    def __init__(self, hbm_budget, max_active=8, chunk_steps=32, n_streams=8, policy=0, short_work=0.0):
         o = _lib.fw_server_opts()
         o.hbm_budget, o.max_active, o.chunk_steps, o.n_streams = int(hbm_budget), int(max_active), \
             int(chunk_steps), int(n_streams)
+        o.policy, o.short_work = int(policy), float(short_work)
         self.h = C.c_void_p()
         check(lib().fw_server_create(C.byref(o), C.byref(self.h)), "fw_server_create")
         self._keep = {}

@@ -60,7 +60,7 @@ class fw_medium_info(C.Structure):
 
 class fw_server_opts(C.Structure):
     _fields_ = [("hbm_budget", C.c_size_t), ("max_active", C.c_int), ("chunk_steps", C.c_int),
-                ("n_streams", C.c_int)]
+                ("n_streams", C.c_int), ("policy", C.c_int), ("short_work", C.c_double)]
 
 
 class fw_request(C.Structure):

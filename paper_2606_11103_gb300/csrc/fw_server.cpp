@@ -8,6 +8,14 @@
 //    resident medium in chunks through its cached CUDA graphs on a pool of
 //    non-blocking streams (two chunks in flight per request), and retires
 //    finished requests (traces out, medium released).
+// Work queue: every chunk launch enqueues the request's tiles (the CTAs of
+// its sweeps) on its stream; the GPU's block scheduler hands free SM slots
+// to the pending tiles of the highest-priority stream first.  The size-class
+// policy (the default) uses three stream priorities: short requests (little
+// work) at the top, so they never wait behind long ones; the oldest running
+// long request in the middle, so the head of the long queue advances at
+// nearly the speed it would have alone; the other long requests at the
+// bottom, filling the slots the others leave idle.
 // All device memory of the media comes from one arena allocated when the
 // server is created, so admission is exact bookkeeping and releasing a
 // medium never calls cudaFree (which would wait for the whole device).
@@ -116,6 +124,8 @@ struct Job {
     double t_submit = 0, t_admit = -1;
     fw_medium *m = nullptr;
     int stream = 0;
+    int level = -1;                // stream priority level of the chunks in flight
+    bool short_job = false;        // voxels x steps <= the server's short_work
     int issued = 0;
     std::deque<cudaEvent_t> inflight;
     bool cancel = false;
@@ -148,8 +158,10 @@ struct fw_server {
     bool stop = false;
     bool debug = false;            // FWGB_SERVER_DEBUG: log builds and failed chunks to stderr
     long long next_id = 1;
-    std::vector<cudaStream_t> streams;
+    std::vector<cudaStream_t> streams;        // kLevels x n_streams, level-major
+    static constexpr int kLevels = 3;         // 0: short requests, 1: oldest long one, 2: other long ones
     std::thread sched, builder;
+    cudaStream_t stream_of(int level, int k) const { return streams[(size_t)level * o.n_streams + k]; }
 
     double now() const
     {
@@ -258,32 +270,49 @@ void fw_server::run_scheduler()
         {
             std::unique_lock<std::mutex> lk(mu);
             if (stop && active.empty() && ready.empty() && to_build.empty() && building == 0) break;
-            // admission: first fit in arrival order; a request skipped too
-            // often blocks the ones behind it
+            // admission: first fit in arrival order (short requests first
+            // under the size-class policy); a request skipped too often
+            // blocks the ones of its class behind it; long requests leave
+            // two slots to short ones when there are four or more slots
             if (!stop) {
-                for (auto it = queue.begin(); it != queue.end();) {
-                    Job *j = *it;
-                    if (j->cancel) {
-                        it = queue.erase(it);
-                        complete(j, FW_CANCELLED, 0.f);
-                        continue;
+                const bool classes = o.policy == 0;
+                int long_used = 0;
+                for (Job *x : active) long_used += !x->short_job;
+                for (Job *x : ready) long_used += !x->short_job;
+                for (Job *x : to_build) long_used += !x->short_job;
+                long_used += building;       // conservatively: builds in progress count as long
+                const int long_cap = classes && o.max_active >= 4 ? o.max_active - 2 : o.max_active;
+                for (int pass = classes ? 0 : 1; pass < 2; ++pass) {
+                    for (auto it = queue.begin(); it != queue.end();) {
+                        Job *j = *it;
+                        if (j->cancel) {
+                            it = queue.erase(it);
+                            complete(j, FW_CANCELLED, 0.f);
+                            continue;
+                        }
+                        if (classes && j->short_job != (pass == 0)) {
+                            ++it;
+                            continue;
+                        }
+                        const int slots = (int)(active.size() + ready.size() + to_build.size()) + building;
+                        if (slots >= o.max_active) break;
+                        if (classes && !j->short_job && long_used >= long_cap) break;
+                        if (j->footprint <= o.hbm_budget - reserved) {
+                            reserved += j->footprint;
+                            j->t_admit = now();
+                            long_used += !j->short_job;
+                            to_build.push_back(j);
+                            it = queue.erase(it);
+                            cv_build.notify_one();
+                            continue;
+                        }
+                        if (++j->skips > FW_SERVER_MAX_SKIPS) break;
+                        ++it;
                     }
-                    const int slots = (int)(active.size() + ready.size() + to_build.size()) + building;
-                    if (slots >= o.max_active) break;
-                    if (j->footprint <= o.hbm_budget - reserved) {
-                        reserved += j->footprint;
-                        j->t_admit = now();
-                        to_build.push_back(j);
-                        it = queue.erase(it);
-                        cv_build.notify_one();
-                        continue;
-                    }
-                    if (++j->skips > FW_SERVER_MAX_SKIPS) break;
-                    ++it;
                 }
             }
             for (Job *j : ready) {
-                j->stream = rr++ % (int)streams.size();
+                j->stream = rr++ % o.n_streams;
                 active.push_back(j);
             }
             ready.clear();
@@ -292,6 +321,10 @@ void fw_server::run_scheduler()
             n_active = (int)active.size();
         }
         bool progress = false;
+        // the oldest long request (lowest id) runs at the middle priority
+        long long oldest_long = -1;
+        for (Job *x : active)
+            if (!x->short_job && (oldest_long < 0 || x->id < oldest_long)) oldest_long = x->id;
         for (size_t k = 0; k < active.size();) {
             Job *j = active[k];
             int status = FW_OK;
@@ -314,7 +347,8 @@ void fw_server::run_scheduler()
                                          x->r.n_steps, x->stream);
                     }
                     cudaGetLastError();
-                    cudaStreamSynchronize(streams[j->stream]);
+                    cudaStreamSynchronize(stream_of(j->level < 0 ? 1 : j->level, j->stream));
+                    if (!j->inflight.empty()) cudaEventSynchronize(j->inflight.back());
                     for (cudaEvent_t x : j->inflight) pool.push_back(x);
                     j->inflight.clear();
                     finished = true;
@@ -327,13 +361,23 @@ void fw_server::run_scheduler()
             }
             while (!finished && !j->cancel && j->issued < j->r.n_steps && j->inflight.size() < 2) {
                 const int n = std::min(o.chunk_steps, j->r.n_steps - j->issued);
-                int rc = fw_run(j->m, n, streams[j->stream]);
+                const int level = o.policy != 0 ? 1 : (j->short_job ? 0 : (j->id == oldest_long ? 1 : 2));
+                cudaStream_t st = stream_of(level, j->stream);
+                int rc = FW_OK;
+                // a request that changes level: its next chunk waits for the last one queued
+                if (j->level >= 0 && level != j->level && !j->inflight.empty() &&
+                    cudaStreamWaitEvent(st, j->inflight.back(), 0) != cudaSuccess)
+                    rc = FW_ERR_CUDA;
+                j->level = level;
+                if (!rc) rc = fw_run(j->m, n, st);
                 cudaEvent_t e = rc ? nullptr : get_event();
-                if (!rc && (!e || cudaEventRecord(e, streams[j->stream]) != cudaSuccess)) rc = FW_ERR_CUDA;
+                if (!rc && (!e || cudaEventRecord(e, st) != cudaSuccess)) rc = FW_ERR_CUDA;
                 if (rc) {
                     if (e) pool.push_back(e);
                     // the chunks already queued must end before the medium goes
-                    cudaStreamSynchronize(streams[j->stream]);
+                    cudaGetLastError();
+                    cudaStreamSynchronize(st);
+                    if (!j->inflight.empty()) cudaEventSynchronize(j->inflight.back());
                     for (cudaEvent_t x : j->inflight) pool.push_back(x);
                     j->inflight.clear();
                     finished = true;
@@ -352,7 +396,8 @@ void fw_server::run_scheduler()
             if (status == FW_OK) {
                 status = fw_status(j->m, &pmax);
                 if ((status == FW_OK || status == FW_ERR_UNSTABLE) && j->r.traces_out && j->m->n_rcv > 0) {
-                    int rc = fw_read_receivers(j->m, j->r.traces_out, 0, streams[j->stream]);
+                    int rc = fw_read_receivers(j->m, j->r.traces_out, 0, stream_of(j->level < 0 ? 1 : j->level,
+                                                                                 j->stream));
                     if (rc) status = rc;
                 }
             }
@@ -380,7 +425,7 @@ extern "C" {
 int fw_server_create(const fw_server_opts *opts, fw_server **out)
 {
     if (!opts || !out || opts->hbm_budget == 0 || opts->max_active < 1 || opts->chunk_steps < 1 ||
-        opts->n_streams < 1)
+        opts->n_streams < 1 || (opts->policy != 0 && opts->policy != 1) || !(opts->short_work >= 0.0))
         return FW_ERR_ARG;
     *out = nullptr;
     fw_server *s = new (std::nothrow) fw_server();
@@ -397,18 +442,28 @@ int fw_server_create(const fw_server_opts *opts, fw_server **out)
         return rc;
     }
     s->o.hbm_budget = s->arena.size();
+    if (s->o.short_work <= 0.0) s->o.short_work = 5e9;
     const char *dbg = std::getenv("FWGB_SERVER_DEBUG");
     s->debug = dbg && *dbg && *dbg != '0';
-    for (int k = 0; k < opts->n_streams; ++k) {
-        cudaStream_t st = nullptr;
-        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
-            cudaGetLastError();
-            for (cudaStream_t x : s->streams) cudaStreamDestroy(x);
-            delete s;
-            return FW_ERR_CUDA;
-        }
-        s->streams.push_back(st);
+    // stream priorities of the three levels: greatest, middle, least of the
+    // device's range (all equal where the device has one level)
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+        cudaGetLastError();
+        least = greatest = 0;
     }
+    const int prio[fw_server::kLevels] = {greatest, (least + greatest) / 2, least};
+    for (int lv = 0; lv < fw_server::kLevels; ++lv)
+        for (int k = 0; k < opts->n_streams; ++k) {
+            cudaStream_t st = nullptr;
+            if (cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, prio[lv]) != cudaSuccess) {
+                cudaGetLastError();
+                for (cudaStream_t x : s->streams) cudaStreamDestroy(x);
+                delete s;
+                return FW_ERR_CUDA;
+            }
+            s->streams.push_back(st);
+        }
     s->t0 = std::chrono::steady_clock::now();
     s->builder = std::thread([s] { s->run_builder(); });
     s->sched = std::thread([s] { s->run_scheduler(); });
@@ -432,6 +487,7 @@ int fw_server_submit(fw_server *s, const fw_request *req, long long *id)
     j->classes.assign(r.classes, r.classes + r.n_classes);
     const size_t n = (size_t)r.grid.nx * r.grid.ny * r.grid.nz;
     j->voxels = (long long)n;
+    j->short_job = (double)n * (double)r.n_steps <= s->o.short_work;
     const long long n_src = r.src_mask ? count_mask(r.src_mask, n) : 0;
     const long long n_rcv = r.rcv_mask ? count_mask(r.rcv_mask, n) : 0;
     const long long n_rec = (r.n_steps + r.decim - 1) / r.decim;

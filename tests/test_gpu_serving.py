@@ -174,3 +174,28 @@ def test_cancel_queued_and_running(fw, lut):
     srv.close()
     assert got[r2]["status"] == fw._lib.FW_CANCELLED and got[r2]["t_admit"] < 0
     assert got[r1]["status"] == fw._lib.FW_CANCELLED
+
+
+@pytest.mark.parametrize("policy", [0, 1])
+def test_short_requests_are_admitted_ahead_of_long_ones(fw, lut, policy):
+    """Size-class policy (0): with one slot, a short request queued behind a
+    long one is admitted first when the slot frees up; in arrival order (1)
+    it waits its turn.  Results are the same either way."""
+    long_q = make_request(lut, (384, 384), seed=50, n_steps=1500)
+    short_q = make_request(lut, (64, 64), seed=51, n_steps=100)
+    srv = fw.Server(hbm_budget=2 << 30, max_active=1, chunk_steps=32, n_streams=2, policy=policy, short_work=1e6)
+    ra, _ = srv.submit(tag=0, **long_q)
+    t_end = time.time() + 30
+    while srv.stats()["active"] == 0 and time.time() < t_end:
+        time.sleep(0.002)
+    rb, _ = srv.submit(tag=1, **long_q)
+    rc, _ = srv.submit(tag=2, **short_q)
+    got = drain(srv, 3)
+    srv.close()
+    assert all(d["status"] == 0 for d in got.values())
+    if policy == 0:
+        assert got[rc]["t_admit"] < got[rb]["t_admit"] and got[rc]["t_done"] < got[rb]["t_done"]
+    else:
+        assert got[rb]["t_admit"] < got[rc]["t_admit"]
+    assert np.array_equal(got[rc]["traces"], run_alone(fw, short_q))
+    assert np.array_equal(got[rb]["traces"], got[ra]["traces"])
