@@ -3,6 +3,8 @@
 #include "fw_internal.h"
 #include "fw_kernels.cuh"
 
+#include <cuda.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -20,6 +22,12 @@ cudaError_t sweeps_f64(const fw_medium *m, cudaStream_t s, int which);
 cudaError_t io_f32(const fw_medium *m, int j, cudaStream_t s);
 cudaError_t io_f64(const fw_medium *m, int j, cudaStream_t s);
 void noalloc_prepare();
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+bool vel_maps_f32(EncodeTiledFn encode, fw_medium *m);
+bool vel_maps_bf16(EncodeTiledFn encode, fw_medium *m);
+bool vel_maps_f16(EncodeTiledFn encode, fw_medium *m);
 }  // namespace fwgb
 
 using namespace fwgb;
@@ -100,6 +108,45 @@ bool is_device_ptr(const void *p)
 double stencil_abs_sum()
 {
     return 1225.0 / 1024.0 + 245.0 / 3072.0 + 49.0 / 5120.0 + 5.0 / 7168.0;
+}
+
+// ---- tensor maps for TMA staging ----------------------------------------------
+// The driver's tensor-map encoder, looked up once through the runtime (no
+// link against the driver library).  Null where it is not available.
+EncodeTiledFn tensor_map_encoder()
+{
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// Tensor maps of the 3D velocity sweep's streams; the sweep falls back to
+// per-thread cp.async staging where they cannot be built (or when the
+// environment sets FWGB_NO_TMA=1, for measurement).
+void setup_tma(fw_medium *m)
+{
+    m->tma = false;
+    if (m->ndim != 3 || m->storage == FW_STORE_F64) return;
+    if (const char *e = std::getenv("FWGB_NO_TMA"))
+        if (*e && *e != '0') return;
+    EncodeTiledFn enc = tensor_map_encoder();
+    if (!enc) return;
+    switch (m->storage) {
+    case FW_STORE_F32: m->tma = vel_maps_f32(enc, m); break;
+    case FW_STORE_BF16: m->tma = vel_maps_bf16(enc, m); break;
+    case FW_STORE_F16: m->tma = vel_maps_f16(enc, m); break;
+    default: break;
+    }
 }
 
 // ---- time-space stencil (Sec. 3.3, after Tan & Huang 2014) -----------------
@@ -696,6 +743,7 @@ int create_common(const fw_grid *g, const float *c, const float *rho, const floa
     m->lut = at(L.lut);
     m->cdev = at(L.cdev);
     m->zseg = choose_zseg(m);
+    setup_tma(m);
     // maps into the padded layout with inheritance
     if (d.es == 8) {
         if ((rc = upload_map(m, (double *)m->cdev, c, s)) || (rc = upload_map(m, (double *)m->rho, rho, s))) { release(m); return rc; }

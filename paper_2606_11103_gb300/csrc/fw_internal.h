@@ -39,6 +39,18 @@ struct Monitor {
     unsigned int max_bits;   // bits of max |p| (non-negative float)
     int nonfinite;
     int bad_index;           // a source/receiver index or step counter out of range (skipped)
+    int timeout;             // a bounded wait of a sweep on its staged copies gave up
+};
+
+// Tensor-map descriptors of the staged streams of the 3D velocity sweep
+// (opaque 128-byte driver objects, built on the host at medium creation):
+// p with its x/y halo box and p own box, v_d, psi1[m][d], rho with its +1
+// halo box and rho own box, the class index and K dt.
+struct alignas(64) TensorMapBlob {
+    unsigned char bytes[128];
+};
+struct VelMaps {
+    TensorMapBlob p_halo, p_own, v[3], psi[FW_MAX_MECH][3], rho_halo, rho_own, cls, kdt;
 };
 
 struct Graph {
@@ -88,4 +100,6 @@ struct fw_medium {
     double psi_pref = 10.0;          // pressure reference [Pa] of binary16 memory variables
     int time_order = 2;              // 2: leapfrog; 4: time-space stencil (Sec. 3.3)
     double ts_a[4][4] = {};          // time-space weights a_m = sum_n ts_a[m][n] r^(2n)
+    bool tma = false;                // 3D velocity sweep staged by tensor-memory-access copies
+    fwgb::VelMaps vel_maps{};
 };

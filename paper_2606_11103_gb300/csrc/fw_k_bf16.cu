@@ -6,4 +6,5 @@ cudaError_t sweeps_bf16(const fw_medium *m, cudaStream_t s, int which)
 {
     return launch_sweeps<float, float, __nv_bfloat16>(m, s, which);
 }
+bool vel_maps_bf16(EncodeTiledFn encode, fw_medium *m) { return build_vel_maps_t<float, float, __nv_bfloat16>(encode, m); }
 }  // namespace fwgb

@@ -4,4 +4,5 @@
 
 namespace fwgb {
 cudaError_t sweeps_f16(const fw_medium *m, cudaStream_t s, int which) { return launch_sweeps<float, float, __half>(m, s, which); }
+bool vel_maps_f16(EncodeTiledFn encode, fw_medium *m) { return build_vel_maps_t<float, float, __half>(encode, m); }
 }  // namespace fwgb

@@ -178,6 +178,64 @@ __device__ __forceinline__ void cp_async4(S *sdst, const S *gsrc, bool ok)
     else { cp_async<16>(sdst, gsrc, ok); cp_async<16>(sdst + 2, gsrc + 2, ok); }
 }
 
+// ---------------------------------------------------------------------------
+// tensor-memory-access (TMA) tile copies completed on an mbarrier
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// make the barrier initialisation visible to the asynchronous (copy) proxy
+__device__ __forceinline__ void mbar_fence_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 " selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok)
+                 : "r"(smem_u32(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase `parity` of bar with a bound on the number of polls;
+// false when the bound was reached (the caller records a timeout).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity)
+{
+    for (unsigned it = 0; it < (1u << 22); ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// order this thread's earlier generic-proxy accesses of shared memory before
+// later asynchronous-proxy writes to it (a buffer refilled by TMA)
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
+// 3D tiled copy of the box at (x, y, z) of the tensor described by map into
+// shared memory at dst (128-byte aligned); x * element size is a multiple of
+// 16 bytes; elements outside the tensor read as zero
+__device__ __forceinline__ void tma_load_3d(void *dst, const TensorMapBlob *map, int x, int y, int z, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(smem_u32(dst)),
+                 "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+                 : "memory");
+}
+
 // 4 consecutive elements of type S from shared memory, as R
 template <typename S> struct Sm;
 template <> struct Sm<float> {
@@ -262,6 +320,8 @@ template <typename R, typename SS, typename SP> struct VelArgs {
     const R *lut;
     const R *pd[3], *pa[3];      // absorbing profile at half points per axis
     const SS *kdt;               // K dt per voxel (time-space stencil only)
+    Monitor *mon;                // failure record (a staged-copy wait that gave up)
+    VelMaps maps;                // tensor maps of the staged streams (TMA staging only)
 };
 
 template <typename R, typename SS, typename SP> struct PresArgs {
@@ -295,7 +355,8 @@ __device__ __forceinline__ void ld4_or_zero(const SS *base, bool ok, R (&v)[4])
 // [BY][4*BX] in the storage type; the derivative tiles (with halos) are
 // double-buffered by plane parity as well.
 
-template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY, bool TS = false> struct VelSmem {
+template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY, bool TS = false, bool TMA = false>
+struct VelSmem {
     static constexpr int TW = 4 * BX, SW = TW + 8, SH = DIM == 3 ? BY + 7 : BY, RO = DIM == 3 ? 3 : 0;
     static constexpr int NAX = DIM == 3 ? 3 : 2;
     static constexpr size_t TILE = (size_t)BY * TW;
@@ -308,10 +369,18 @@ template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY,
     static constexpr size_t o_pml = o_cls + (TILE * 2 + 15) / 16 * 16;     // absorbing-layer psi per axis
     static constexpr size_t o_kv = o_pml + 3 * TILE * sizeof(SS);          // K dt of plane k (time-space only)
     static constexpr size_t stage = (o_kv + (TS ? TILE * sizeof(SS) : 0) + 127) / 128 * 128;
-    // derivative tiles
+    // derivative tiles of p (x/y halos) and rho (+1 halos), two each; every
+    // buffer starts on 128 bytes (TMA destinations)
+    static constexpr size_t sp_stride = ((size_t)SH * SW * sizeof(R) + 127) / 128 * 128;
+    static constexpr size_t sr_stride = ((size_t)(BY + 1) * (TW + 4) * sizeof(R) + 127) / 128 * 128;
     static constexpr size_t o_sp = 2 * stage;
-    static constexpr size_t o_sr = o_sp + 2 * (size_t)SH * SW * sizeof(R);
-    static constexpr size_t bytes = o_sr + 2 * (size_t)(BY + 1) * (TW + 4) * sizeof(R);
+    static constexpr size_t o_sr = o_sp + 2 * sp_stride;
+    static constexpr size_t o_bar = o_sr + 2 * sr_stride;                   // two mbarriers (TMA staging)
+    static constexpr size_t bytes = o_bar + (TMA ? 16 : 0);
+    // bytes the TMA copies of one plane deliver (completion count of its barrier)
+    static constexpr unsigned tma_bytes =
+        (unsigned)(((size_t)SH * SW + (size_t)(BY + 1) * (TW + 4)) * sizeof(SS) +
+                   TILE * (5 + (TS ? 1 : 0)) * sizeof(SS) + (size_t)NM * 3 * TILE * sizeof(SP) + TILE * 2);
 };
 
 template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY, bool TS = false> struct PresSmem {
@@ -334,16 +403,55 @@ template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY,
 // ---------------------------------------------------------------------------
 // velocity sweep
 
-template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY, bool TS>
+// TMA staging of plane k (3D): one thread arms the stage's barrier with the
+// byte count and issues one tile copy per stream; the copies of the p tile
+// (x/y halos and corners included) and of the rho tile (+1 halos) land in
+// the derivative buffers of parity k&1
+template <typename R, typename SS, typename SP, int NM, int BX, int BY, bool TS>
+__device__ __forceinline__ void vel_issue_tma(const VelArgs<R, SS, SP> &A, unsigned char *sm, int k, int xb, int yb)
+{
+    using L = VelSmem<R, SS, SP, 3, NM, BX, BY, TS, true>;
+    unsigned char *st = sm + (k & 1) * L::stage;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + L::o_bar) + (k & 1);
+    fence_proxy_async_smem();
+    mbar_expect_tx(bar, L::tma_bytes);
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        tma_load_3d(st + L::o_v + ax * L::TILE * sizeof(SS), &A.maps.v[ax], xb, yb, k, bar);
+#pragma unroll
+        for (int m = 0; m < NM; ++m)
+            tma_load_3d(st + L::o_psi + (m * 3 + ax) * L::TILE * sizeof(SP), &A.maps.psi[m][ax], xb, yb, k, bar);
+    }
+    tma_load_3d(st + L::o_pn, &A.maps.p_own, xb, yb, k + 4, bar);
+    tma_load_3d(st + L::o_rn, &A.maps.rho_own, xb, yb, k + 1, bar);
+    tma_load_3d(st + L::o_cls, &A.maps.cls, xb, yb, k, bar);
+    if (TS) tma_load_3d(st + L::o_kv, &A.maps.kdt, xb, yb, k, bar);
+    tma_load_3d(sm + L::o_sp + (k & 1) * L::sp_stride, &A.maps.p_halo, xb - 4, yb - L::RO, k, bar);
+    tma_load_3d(sm + L::o_sr + (k & 1) * L::sr_stride, &A.maps.rho_halo, xb, yb, k, bar);
+}
+
+template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY, bool TS, bool TMA>
 __device__ __forceinline__ void vel_issue(const VelArgs<R, SS, SP> &A, unsigned char *sm, int k, int x0, int y,
                                           int xb, int yb, long long row, bool hd)
 {
-    using L = VelSmem<R, SS, SP, DIM, NM, BX, BY, TS>;
+    using L = VelSmem<R, SS, SP, DIM, NM, BX, BY, TS, TMA>;
     const Geo<R> &G = A.g;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const long long pk = (long long)k * G.plane;
     unsigned char *st = sm + (k & 1) * L::stage;
     const int e0 = ty * L::TW + 4 * tx;       // this thread's element offset in a stage tile
+    if (TMA) {
+        if (tx == 0 && ty == 0) vel_issue_tma<R, SS, SP, NM, BX, BY, TS>(A, sm, k, xb, yb);
+        // absorbing-layer memory: per thread, where this thread needs it
+        if (G.wabs > 0 && hd) {
+            const bool in[3] = {x0 < G.wabs || x0 + 3 >= G.nx - G.wabs, y < G.wabs || y >= G.ny - G.wabs,
+                                k < G.wabs || k >= G.nz - G.wabs};
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax)
+                if (in[ax]) cp_async4(reinterpret_cast<SS *>(st + L::o_pml) + ax * L::TILE + e0, A.psip[ax] + pk + row, true);
+        }
+        return;
+    }
     const SS *gz = A.p;                       // any valid address for zero-fill copies
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
@@ -370,8 +478,8 @@ __device__ __forceinline__ void vel_issue(const VelArgs<R, SS, SP> &A, unsigned 
             if (in[ax]) cp_async4(reinterpret_cast<SS *>(st + L::o_pml) + ax * L::TILE + e0, A.psip[ax] + pk + row, true);
     }
     // halos of plane k straight into the derivative tiles of parity k&1
-    R *sp = reinterpret_cast<R *>(sm + L::o_sp) + (k & 1) * L::SH * L::SW;
-    R *sr = reinterpret_cast<R *>(sm + L::o_sr) + (k & 1) * (BY + 1) * (L::TW + 4);
+    R *sp = reinterpret_cast<R *>(sm + L::o_sp + (k & 1) * L::sp_stride);
+    R *sr = reinterpret_cast<R *>(sm + L::o_sr + (k & 1) * L::sr_stride);
     if (tx == 0) {
         const bool ok = y < G.ny && x0 - 4 >= 0;
         cp_async4(reinterpret_cast<SS *>(sp + (L::RO + ty) * L::SW), ok ? A.p + pk + (long long)y * G.px + (x0 - 4) : gz, ok);
@@ -512,12 +620,13 @@ __device__ __forceinline__ void vel_gradient_ts(const VelArgs<R, SS, SP> &A, con
 
 // 3D: 32-bit memory variables fill shared memory at two CTAs per SM, 16-bit
 // ones fit three (registers are held to the matching share)
-template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY, bool TS>
+template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY, bool TS, bool TMA>
 __global__ void __launch_bounds__(BX *BY, DIM == 3 ? ((BY < 8 && sizeof(SP) == 2 && !TS) ? 3 : 2) : 1)
-k_velocity(const VelArgs<R, SS, SP> A)
+k_velocity(const __grid_constant__ VelArgs<R, SS, SP> A)
 {
-    using L = VelSmem<R, SS, SP, DIM, NM, BX, BY, TS>;
-    constexpr int TW = L::TW, SW = L::SW, SH = L::SH, RO = L::RO;
+    static_assert(!TMA || DIM == 3, "TMA staging is built for the 3D sweep");
+    using L = VelSmem<R, SS, SP, DIM, NM, BX, BY, TS, TMA>;
+    constexpr int TW = L::TW, SW = L::SW, RO = L::RO;
     static_assert(sizeof(SS) == sizeof(R), "state is stored in the arithmetic type");
     extern __shared__ __align__(128) unsigned char smem[];
 
@@ -539,7 +648,17 @@ k_velocity(const VelArgs<R, SS, SP> A)
         ld4_or_zero(A.p + kk * G.plane + row, hd && kk >= 0 && kk < G.nz, q[j]);
     }
     ld4_or_zero(A.rho + z0 * G.plane + row, hd && z0 < G.nz, rq[0]);
-    if (z0 < z1) vel_issue<R, SS, SP, DIM, NM, BX, BY, TS>(A, smem, z0, x0, y, xb, yb, row, hd);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L::o_bar);
+    if (TMA) {
+        if (tx == 0 && ty == 0) {
+            mbar_init(bars, 1);
+            mbar_init(bars + 1, 1);
+            mbar_fence_init();
+        }
+        __syncthreads();
+    }
+    bool timed_out = false;
+    if (z0 < z1) vel_issue<R, SS, SP, DIM, NM, BX, BY, TS, TMA>(A, smem, z0, x0, y, xb, yb, row, hd);
     cp_commit();
     // absorbing-layer profile of this thread's x and y positions (fixed over the march)
     const bool pml_x = G.wabs > 0 && (x0 < G.wabs || x0 + 3 >= G.nx - G.wabs);
@@ -567,21 +686,25 @@ k_velocity(const VelArgs<R, SS, SP> A)
         const long long pk = (long long)k * G.plane;
         const int buf = k & 1;
         unsigned char *st = smem + buf * L::stage;
-        R(*sp)[SW] = reinterpret_cast<R(*)[SW]>(smem + L::o_sp + buf * (size_t)SH * SW * sizeof(R));
-        R(*sr)[TW + 4] = reinterpret_cast<R(*)[TW + 4]>(smem + L::o_sr + buf * (size_t)(BY + 1) * (TW + 4) * sizeof(R));
+        R(*sp)[SW] = reinterpret_cast<R(*)[SW]>(smem + L::o_sp + buf * L::sp_stride);
+        R(*sr)[TW + 4] = reinterpret_cast<R(*)[TW + 4]>(smem + L::o_sr + buf * L::sr_stride);
         __syncthreads();                           // iteration k-1 is done with stage/tiles (k+1)&1
-        {
+        if (!TMA) {                                // centre of the tiles from registers (TMA copies them)
             R *dst = &sp[RO + ty][4 + 4 * tx];
             dst[0] = q[3][0]; dst[1] = q[3][1]; dst[2] = q[3][2]; dst[3] = q[3][3];
             R *r = &sr[ty][4 * tx];
             r[0] = rq[0][0]; r[1] = rq[0][1]; r[2] = rq[0][2]; r[3] = rq[0][3];
         }
-        if (k + 1 < z1) vel_issue<R, SS, SP, DIM, NM, BX, BY, TS>(A, smem, k + 1, x0, y, xb, yb, row, hd);
+        if (k + 1 < z1) vel_issue<R, SS, SP, DIM, NM, BX, BY, TS, TMA>(A, smem, k + 1, x0, y, xb, yb, row, hd);
         cp_commit();
         const bool pml_z = G.wabs > 0 && (k < G.wabs || k >= G.nz - G.wabs);
         R pdz = 0, paz = 0;
         if (pml_z) { pdz = A.pd[2][k]; paz = A.pa[2][k]; }
         cp_wait<1>();                              // this thread's copies of plane k have landed
+        // bounded wait for the TMA copies of plane k; after a timeout the
+        // thread stops waiting (the sweep then ends quickly, its result
+        // flagged on the monitor)
+        if (TMA && !timed_out && !mbar_wait_bounded(bars + buf, (unsigned)((k - z0) >> 1) & 1u)) timed_out = true;
         __syncthreads();                           // ... and everyone's
         Sm<SS>::ld(reinterpret_cast<const SS *>(st + L::o_pn) + e0, q[7]);
         Sm<SS>::ld(reinterpret_cast<const SS *>(st + L::o_rn) + e0, rq[1]);
@@ -716,6 +839,12 @@ k_velocity(const VelArgs<R, SS, SP> A)
         for (int e = 0; e < 4; ++e) rq[0][e] = rq[1][e];
     }
     cp_wait<0>();
+    if (TMA && timed_out) {
+        // record the failure; give the copies of the last two planes one more
+        // bounded chance to land before the CTA's shared memory is released
+        atomicExch(&A.mon->timeout, 1);
+        for (int k = max(z0, z1 - 2); k < z1; ++k) mbar_wait_bounded(bars + (k & 1), (unsigned)((k - z0) >> 1) & 1u);
+    }
 }
 
 // ---------------------------------------------------------------------------

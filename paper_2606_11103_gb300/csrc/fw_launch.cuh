@@ -5,6 +5,8 @@
 
 #include "fw_kernels.cuh"
 
+#include <cuda.h>
+
 namespace fwgb {
 
 // rows of the 3D CTA tiles (tuning knobs, measured best): the velocity sweep
@@ -45,6 +47,55 @@ template <typename R> Geo<R> make_geo(const fw_medium *m)
     return g;
 }
 
+// Tensor maps of the streams the 3D velocity sweep stages by TMA: every
+// array is addressed as a 3D tensor (px, NY, NZ) with the medium's pitches;
+// boxes are the CTA tile (TW x BY) or its halo boxes (p: (TW+8) x (BY+7)
+// from (xb-4, yb-3); rho: (TW+4) x (BY+1) from (xb, yb)).  Elements outside
+// the tensor read as zero.  encode is the driver's tensor-map encoder.
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+template <typename T> constexpr CUtensorMapDataType map_type();
+template <> constexpr CUtensorMapDataType map_type<float>() { return CU_TENSOR_MAP_DATA_TYPE_FLOAT32; }
+template <> constexpr CUtensorMapDataType map_type<__nv_bfloat16>() { return CU_TENSOR_MAP_DATA_TYPE_BFLOAT16; }
+template <> constexpr CUtensorMapDataType map_type<__half>() { return CU_TENSOR_MAP_DATA_TYPE_FLOAT16; }
+template <> constexpr CUtensorMapDataType map_type<uint16_t>() { return CU_TENSOR_MAP_DATA_TYPE_UINT16; }
+
+template <typename T>
+bool encode_map(EncodeTiledFn encode, TensorMapBlob *out, const fw_medium *m, const void *base, unsigned bx,
+                unsigned by)
+{
+    const cuuint64_t dims[3] = {(cuuint64_t)m->px, (cuuint64_t)m->NY, (cuuint64_t)m->NZ};
+    const cuuint64_t strides[2] = {(cuuint64_t)m->px * sizeof(T), (cuuint64_t)m->plane * sizeof(T)};
+    const cuuint32_t box[3] = {bx, by, 1}, estr[3] = {1, 1, 1};
+    return encode(reinterpret_cast<CUtensorMap *>(out), map_type<T>(), 3, const_cast<void *>(base), dims, strides,
+                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <typename R, typename SS, typename SP>
+bool build_vel_maps_t(EncodeTiledFn encode, fw_medium *m)
+{
+    if constexpr (sizeof(R) != 4) {
+        return false;
+    } else {
+        constexpr int TW = 4 * Tile3<R>::BX, BY = Tile3<R>::BYV;
+        VelMaps &v = m->vel_maps;
+        bool ok = encode_map<SS>(encode, &v.p_halo, m, m->p, TW + 8, BY + 7) &&
+                  encode_map<SS>(encode, &v.p_own, m, m->p, TW, BY) &&
+                  encode_map<SS>(encode, &v.rho_halo, m, m->rho, TW + 4, BY + 1) &&
+                  encode_map<SS>(encode, &v.rho_own, m, m->rho, TW, BY) &&
+                  encode_map<uint16_t>(encode, &v.cls, m, m->cls, TW, BY) &&
+                  encode_map<SS>(encode, &v.kdt, m, m->kdt, TW, BY);
+        for (int ax = 0; ax < 3 && ok; ++ax) {
+            ok = encode_map<SS>(encode, &v.v[ax], m, m->v[ax], TW, BY);
+            for (int n = 0; n < m->nmech && ok; ++n) ok = encode_map<SP>(encode, &v.psi[n][ax], m, m->psi1[n][ax], TW, BY);
+        }
+        return ok;
+    }
+}
+
 // which: bit 0 = velocity sweep, bit 1 = pressure sweep, bit 2 = only opt the
 // instances into their dynamic shared memory (done once at medium creation,
 // outside any stream capture)
@@ -54,11 +105,19 @@ cudaError_t launch_dn(const fw_medium *m, cudaStream_t s, int which)
     constexpr int BX = DIM == 3 ? Tile3<R>::BX : Tile2<R>::BX;
     constexpr int BYV = DIM == 3 ? Tile3<R>::BYV : Tile2<R>::BYV;
     constexpr int BYP = DIM == 3 ? Tile3<R>::BYP : Tile2<R>::BYP;
+    // the 3D FP32-state velocity sweep stages its streams by TMA when the
+    // medium holds tensor maps for them (the cp.async instance otherwise)
+    constexpr bool CAN_TMA = DIM == 3 && sizeof(R) == 4;
     using LV = VelSmem<R, SS, SP, DIM, NM, BX, BYV, TS>;
+    using LVT = VelSmem<R, SS, SP, DIM, NM, BX, BYV, TS, CAN_TMA>;
     using LP = PresSmem<R, SS, SP, DIM, NM, BX, BYP, TS>;
     if (which & 4) {
-        cudaError_t e = cudaFuncSetAttribute(k_velocity<R, SS, SP, DIM, NM, BX, BYV, TS>,
+        cudaError_t e = cudaFuncSetAttribute(k_velocity<R, SS, SP, DIM, NM, BX, BYV, TS, false>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LV::bytes);
+        if constexpr (CAN_TMA)
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_velocity<R, SS, SP, DIM, NM, BX, BYV, TS, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LVT::bytes);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_pressure<R, SS, SP, DIM, NM, BX, BYP, true, TS>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LP::bytes);
@@ -84,8 +143,19 @@ cudaError_t launch_dn(const fw_medium *m, cudaStream_t s, int which)
     va.cls = m->cls;
     va.lut = static_cast<const R *>(m->lut);
     va.kdt = static_cast<const SS *>(m->kdt);
-    if (which & 1)
-        k_velocity<R, SS, SP, DIM, NM, BX, BYV, TS><<<dim3(gx, (m->NY + BYV - 1) / BYV, gz), dim3(BX, BYV), LV::bytes, s>>>(va);
+    va.mon = m->mon;
+    if (which & 1) {
+        const dim3 gv(gx, (m->NY + BYV - 1) / BYV, gz), bv(BX, BYV);
+        bool done = false;
+        if constexpr (CAN_TMA) {
+            if (m->tma) {
+                va.maps = m->vel_maps;
+                k_velocity<R, SS, SP, DIM, NM, BX, BYV, TS, true><<<gv, bv, LVT::bytes, s>>>(va);
+                done = true;
+            }
+        }
+        if (!done) k_velocity<R, SS, SP, DIM, NM, BX, BYV, TS, false><<<gv, bv, LV::bytes, s>>>(va);
+    }
     if (!(which & 2)) return cudaGetLastError();
 
     PresArgs<R, SS, SP> pa{};

@@ -78,8 +78,9 @@ def sweep(n_pairs=None):
             r = np.array(refl)
             out[(ramp, cfg)] = (float(np.median(r)) if r.size else math.nan,
                                 100.0 * float(np.mean(r < -50.0)) if r.size else math.nan, bad, len(pairs))
-            print("%-12s %-8s median R %6.1f dB, %5.1f %% below -50 dB, %2d of %d unstable   (paper %.1f, %.1f %%, %d)"
-                  % (("ramped" if ramp else "full strength"), cfg) + out[(ramp, cfg)] + PAPER[cfg], flush=True)
+            row = (("ramped" if ramp else "full strength"), cfg) + out[(ramp, cfg)] + PAPER[cfg]
+            print("%-13s %-8s median R %6.1f dB, %5.1f %% below -50 dB, %2d of %d unstable   (paper %.1f, %.1f %%, %d)"
+                  % row, flush=True)
     return out
 
 
