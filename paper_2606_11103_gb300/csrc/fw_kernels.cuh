@@ -375,8 +375,12 @@ struct VelSmem {
     static constexpr size_t sr_stride = ((size_t)(BY + 1) * (TW + 4) * sizeof(R) + 127) / 128 * 128;
     static constexpr size_t o_sp = 2 * stage;
     static constexpr size_t o_sr = o_sp + 2 * sp_stride;
-    static constexpr size_t o_bar = o_sr + 2 * sr_stride;                   // two mbarriers (TMA staging)
-    static constexpr size_t bytes = o_bar + (TMA ? 16 : 0);
+    // two mbarriers (TMA staging) in the padding after the second rho tile,
+    // which its copies do not reach: the layout's size is that of the
+    // cp.async variant, so both fit the same number of CTAs per SM
+    static constexpr size_t o_bar = o_sr + sr_stride + ((size_t)(BY + 1) * (TW + 4) * sizeof(R) + 7) / 8 * 8;
+    static_assert(o_bar + 16 <= o_sr + 2 * sr_stride, "no room for the barriers in the rho tile padding");
+    static constexpr size_t bytes = o_sr + 2 * sr_stride;
     // bytes the TMA copies of one plane deliver (completion count of its barrier)
     static constexpr unsigned tma_bytes =
         (unsigned)(((size_t)SH * SW + (size_t)(BY + 1) * (TW + 4)) * sizeof(SS) +
