@@ -52,6 +52,12 @@ struct alignas(64) TensorMapBlob {
 struct VelMaps {
     TensorMapBlob p_halo, p_own, v[3], psi[FW_MAX_MECH][3], rho_halo, rho_own, cls, kdt;
 };
+// ... and of the 3D pressure sweep: v_z own box (planes ahead), v_x with its
+// x halo, v_y with its y halo, p, K dt, 2 beta dt, psi2[m], the class index,
+// rho (time-space stencil)
+struct PresMaps {
+    TensorMapBlob vz_own, vx_halo, vy_halo, p_own, kdt, b2dt, psi[FW_MAX_MECH], cls, rho_own;
+};
 
 struct Graph {
     cudaGraph_t graph = nullptr;
@@ -100,6 +106,7 @@ struct fw_medium {
     double psi_pref = 10.0;          // pressure reference [Pa] of binary16 memory variables
     int time_order = 2;              // 2: leapfrog; 4: time-space stencil (Sec. 3.3)
     double ts_a[4][4] = {};          // time-space weights a_m = sum_n ts_a[m][n] r^(2n)
-    bool tma = false;                // 3D velocity sweep staged by tensor-memory-access copies
+    bool tma = false;                // 3D sweeps staged by tensor-memory-access copies
     fwgb::VelMaps vel_maps{};
+    fwgb::PresMaps pres_maps{};
 };

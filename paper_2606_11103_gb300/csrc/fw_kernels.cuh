@@ -337,6 +337,7 @@ template <typename R, typename SS, typename SP> struct PresArgs {
     const R *pd[3], *pa[3];      // absorbing profile at integer points per axis
     Monitor *mon;
     const SS *rho;               // density per voxel (time-space stencil only)
+    PresMaps maps;               // tensor maps of the staged streams (TMA staging only)
 };
 
 template <typename SS, typename R>
@@ -387,7 +388,8 @@ struct VelSmem {
                    TILE * (5 + (TS ? 1 : 0)) * sizeof(SS) + (size_t)NM * 3 * TILE * sizeof(SP) + TILE * 2);
 };
 
-template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY, bool TS = false> struct PresSmem {
+template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY, bool TS = false, bool TMA = false>
+struct PresSmem {
     static constexpr int TW = 4 * BX, SWX = TW + 8, SHY = DIM == 3 ? BY + 7 : 1;
     static constexpr size_t TILE = (size_t)BY * TW;
     static constexpr size_t o_qn = 0;
@@ -399,9 +401,13 @@ template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY,
     static constexpr size_t o_pml = o_cls + (TILE * 2 + 15) / 16 * 16;
     static constexpr size_t o_rh = o_pml + 3 * TILE * sizeof(SS);          // rho of plane k (time-space only)
     static constexpr size_t stage = (o_rh + (TS ? TILE * sizeof(SS) : 0) + 127) / 128 * 128;
+    // v_x (x halo) and v_y (y halo) tiles, two each, on 128-byte boundaries
+    static constexpr size_t svx_stride = ((size_t)BY * SWX * sizeof(R) + 127) / 128 * 128;
+    static constexpr size_t svy_stride = ((size_t)SHY * TW * sizeof(R) + 127) / 128 * 128;
     static constexpr size_t o_svx = 2 * stage;
-    static constexpr size_t o_svy = o_svx + 2 * (size_t)BY * SWX * sizeof(R);
-    static constexpr size_t bytes = o_svy + 2 * (size_t)SHY * TW * sizeof(R);
+    static constexpr size_t o_svy = o_svx + 2 * svx_stride;
+    static constexpr size_t o_bar = o_svy + 2 * svy_stride;                 // two mbarriers (TMA staging)
+    static constexpr size_t bytes = o_bar + (TMA ? 16 : 0);
 };
 
 // ---------------------------------------------------------------------------
@@ -709,7 +715,10 @@ k_velocity(const __grid_constant__ VelArgs<R, SS, SP> A)
         // thread stops waiting (the sweep then ends quickly, its result
         // flagged on the monitor)
         if (TMA && !timed_out && !mbar_wait_bounded(bars + buf, (unsigned)((k - z0) >> 1) & 1u)) timed_out = true;
-        __syncthreads();                           // ... and everyone's
+        // cp.async staging: everyone's copies and tile centres visible to all.
+        // TMA staging: every thread has waited on the barrier itself and
+        // reads only its own cp.async copies (absorbing layer), so no barrier
+        if (!TMA) __syncthreads();
         Sm<SS>::ld(reinterpret_cast<const SS *>(st + L::o_pn) + e0, q[7]);
         Sm<SS>::ld(reinterpret_cast<const SS *>(st + L::o_rn) + e0, rq[1]);
         if (hd) {
@@ -854,16 +863,54 @@ k_velocity(const __grid_constant__ VelArgs<R, SS, SP> A)
 // ---------------------------------------------------------------------------
 // pressure sweep
 
-template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY, bool NL, bool TS>
+// TMA staging of plane k of the pressure sweep (3D): one thread arms the
+// stage's barrier and issues one tile copy per stream; v_x (x halo) and v_y
+// (y halo) land in the tiles of parity k&1
+template <typename R, typename SS, typename SP, int NM, int BX, int BY, bool NL, bool TS>
+__device__ __forceinline__ void pres_issue_tma(const PresArgs<R, SS, SP> &A, unsigned char *sm, int k, int xb, int yb)
+{
+    using L = PresSmem<R, SS, SP, 3, NM, BX, BY, TS, true>;
+    constexpr unsigned bytes = (unsigned)(((size_t)BY * L::SWX + (size_t)L::SHY * L::TW) * sizeof(SS) +
+                                          L::TILE * (3 + (NL ? 1 : 0) + (TS ? 1 : 0)) * sizeof(SS) +
+                                          (size_t)NM * L::TILE * sizeof(SP) + L::TILE * 2);
+    unsigned char *st = sm + (k & 1) * L::stage;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + L::o_bar) + (k & 1);
+    fence_proxy_async_smem();
+    mbar_expect_tx(bar, bytes);
+    tma_load_3d(st + L::o_qn, &A.maps.vz_own, xb, yb, k + 3, bar);
+    tma_load_3d(st + L::o_p, &A.maps.p_own, xb, yb, k, bar);
+    tma_load_3d(st + L::o_kd, &A.maps.kdt, xb, yb, k, bar);
+    if (NL) tma_load_3d(st + L::o_bd, &A.maps.b2dt, xb, yb, k, bar);
+    if (TS) tma_load_3d(st + L::o_rh, &A.maps.rho_own, xb, yb, k, bar);
+#pragma unroll
+    for (int m = 0; m < NM; ++m) tma_load_3d(st + L::o_psi + m * L::TILE * sizeof(SP), &A.maps.psi[m], xb, yb, k, bar);
+    tma_load_3d(st + L::o_cls, &A.maps.cls, xb, yb, k, bar);
+    tma_load_3d(sm + L::o_svx + (k & 1) * L::svx_stride, &A.maps.vx_halo, xb - 4, yb, k, bar);
+    tma_load_3d(sm + L::o_svy + (k & 1) * L::svy_stride, &A.maps.vy_halo, xb, yb - 4, k, bar);
+}
+
+template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY, bool NL, bool TS, bool TMA>
 __device__ __forceinline__ void pres_issue(const PresArgs<R, SS, SP> &A, unsigned char *sm, int k, int x0, int y,
                                            int yb, long long row, bool hd)
 {
-    using L = PresSmem<R, SS, SP, DIM, NM, BX, BY, TS>;
+    using L = PresSmem<R, SS, SP, DIM, NM, BX, BY, TS, TMA>;
     const Geo<R> &G = A.g;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const long long pk = (long long)k * G.plane;
     unsigned char *st = sm + (k & 1) * L::stage;
     const int e0 = ty * L::TW + 4 * tx;
+    if (TMA) {
+        if (tx == 0 && ty == 0) pres_issue_tma<R, SS, SP, NM, BX, BY, NL, TS>(A, sm, k, x0, yb);
+        // absorbing-layer memory: per thread, where this thread needs it
+        if (G.wabs > 0 && hd) {
+            const bool in[3] = {x0 < G.wabs || x0 + 3 >= G.nx - G.wabs, y < G.wabs || y >= G.ny - G.wabs,
+                                k < G.wabs || k >= G.nz - G.wabs};
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax)
+                if (in[ax]) cp_async4(reinterpret_cast<SS *>(st + L::o_pml) + ax * L::TILE + e0, A.psip[ax] + pk + row, true);
+        }
+        return;
+    }
     const SS *gz = A.p;
     {
         const bool ok = hd && k + 3 < G.nz;
@@ -886,7 +933,7 @@ __device__ __forceinline__ void pres_issue(const PresArgs<R, SS, SP> &A, unsigne
             if (in[ax]) cp_async4(reinterpret_cast<SS *>(st + L::o_pml) + ax * L::TILE + e0, A.psip[ax] + pk + row, true);
     }
     // v_x (with x halo) and v_y (with y halo) of plane k straight into the tiles
-    R *svx = reinterpret_cast<R *>(sm + L::o_svx) + (k & 1) * BY * L::SWX;
+    R *svx = reinterpret_cast<R *>(sm + L::o_svx + (k & 1) * L::svx_stride);
     cp_async4(reinterpret_cast<SS *>(svx + ty * L::SWX + 4 + 4 * tx), hd ? A.v[0] + pk + row : gz, hd);
     if (tx == 0) {
         const bool ok = y < G.ny && x0 - 4 >= 0;
@@ -897,7 +944,7 @@ __device__ __forceinline__ void pres_issue(const PresArgs<R, SS, SP> &A, unsigne
         cp_async4(reinterpret_cast<SS *>(svx + ty * L::SWX + L::TW + 4), ok ? A.v[0] + pk + (long long)y * G.px + (x0 + 4) : gz, ok);
     }
     if (DIM == 3) {
-        R *svy = reinterpret_cast<R *>(sm + L::o_svy) + (k & 1) * L::SHY * L::TW;
+        R *svy = reinterpret_cast<R *>(sm + L::o_svy + (k & 1) * L::svy_stride);
         cp_async4(reinterpret_cast<SS *>(svy + (4 + ty) * L::TW + 4 * tx), hd ? A.v[1] + pk + row : gz, hd);
         for (int r = ty; r < 7; r += BY) {      // 4 halo rows below the tile, 3 above
             const int yy = r < 4 ? yb - 4 + r : yb + BY + (r - 4);
@@ -1019,11 +1066,12 @@ __device__ __forceinline__ void pres_divergence_ts(const PresArgs<R, SS, SP> &A,
     }
 }
 
-template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY, bool NL, bool TS>
+template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY, bool NL, bool TS, bool TMA>
 __global__ void __launch_bounds__(BX *BY, DIM == 3 ? ((BY < 8 && !TS) ? 3 : 2) : 1)
-k_pressure(const PresArgs<R, SS, SP> A)
+k_pressure(const __grid_constant__ PresArgs<R, SS, SP> A)
 {
-    using L = PresSmem<R, SS, SP, DIM, NM, BX, BY, TS>;
+    static_assert(!TMA || DIM == 3, "TMA staging is built for the 3D sweep");
+    using L = PresSmem<R, SS, SP, DIM, NM, BX, BY, TS, TMA>;
     constexpr int TW = L::TW, SWX = L::SWX, SHY = L::SHY;
     extern __shared__ __align__(128) unsigned char smem[];
 
@@ -1045,7 +1093,17 @@ k_pressure(const PresArgs<R, SS, SP> A)
     }
     R pmax = R(0);
     bool bad = false;
-    if (z0 < z1) pres_issue<R, SS, SP, DIM, NM, BX, BY, NL, TS>(A, smem, z0, x0, y, yb, row, hd);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L::o_bar);
+    if (TMA) {
+        if (tx == 0 && ty == 0) {
+            mbar_init(bars, 1);
+            mbar_init(bars + 1, 1);
+            mbar_fence_init();
+        }
+        __syncthreads();
+    }
+    bool timed_out = false;
+    if (z0 < z1) pres_issue<R, SS, SP, DIM, NM, BX, BY, NL, TS, TMA>(A, smem, z0, x0, y, yb, row, hd);
     cp_commit();
     const bool pml_x = G.wabs > 0 && (x0 < G.wabs || x0 + 3 >= G.nx - G.wabs);
     const bool pml_y = DIM == 3 && G.wabs > 0 && (y < G.wabs || y >= G.ny - G.wabs);
@@ -1068,16 +1126,19 @@ k_pressure(const PresArgs<R, SS, SP> A)
         const long long pk = (long long)k * G.plane;
         const int buf = k & 1;
         unsigned char *st = smem + buf * L::stage;
-        const R(*svx)[SWX] = reinterpret_cast<const R(*)[SWX]>(smem + L::o_svx + buf * (size_t)BY * SWX * sizeof(R));
-        const R(*svy)[TW] = reinterpret_cast<const R(*)[TW]>(smem + L::o_svy + buf * (size_t)SHY * TW * sizeof(R));
+        const R(*svx)[SWX] = reinterpret_cast<const R(*)[SWX]>(smem + L::o_svx + buf * L::svx_stride);
+        const R(*svy)[TW] = reinterpret_cast<const R(*)[TW]>(smem + L::o_svy + buf * L::svy_stride);
         __syncthreads();
-        if (k + 1 < z1) pres_issue<R, SS, SP, DIM, NM, BX, BY, NL, TS>(A, smem, k + 1, x0, y, yb, row, hd);
+        if (k + 1 < z1) pres_issue<R, SS, SP, DIM, NM, BX, BY, NL, TS, TMA>(A, smem, k + 1, x0, y, yb, row, hd);
         cp_commit();
         const bool pml_z = G.wabs > 0 && (k < G.wabs || k >= G.nz - G.wabs);
         R pdz = 0, paz = 0;
         if (pml_z) { pdz = A.pd[2][k]; paz = A.pa[2][k]; }
         cp_wait<1>();
-        __syncthreads();
+        // bounded wait for the TMA copies of plane k (see the velocity sweep);
+        // with TMA staging each thread has waited itself: no barrier needed
+        if (TMA && !timed_out && !mbar_wait_bounded(bars + buf, (unsigned)((k - z0) >> 1) & 1u)) timed_out = true;
+        if (!TMA) __syncthreads();
         Sm<SS>::ld(reinterpret_cast<const SS *>(st + L::o_qn) + e0, qz[7]);
         if (hd) {
             R qd[3][4];
@@ -1204,6 +1265,10 @@ k_pressure(const PresArgs<R, SS, SP> A)
             for (int e = 0; e < 4; ++e) qz[j][e] = qz[j + 1][e];
     }
     cp_wait<0>();
+    if (TMA && timed_out) {
+        atomicExch(&A.mon->timeout, 1);
+        for (int k = max(z0, z1 - 2); k < z1; ++k) mbar_wait_bounded(bars + (k & 1), (unsigned)((k - z0) >> 1) & 1u);
+    }
     // ---- stability monitor: one atomic per warp ----
     float m = bad ? 0.0f : (float)fmin(pmax, R(3.0e38));
     unsigned any_bad = __ballot_sync(0xffffffffu, bad);

@@ -92,6 +92,18 @@ bool build_vel_maps_t(EncodeTiledFn encode, fw_medium *m)
             ok = encode_map<SS>(encode, &v.v[ax], m, m->v[ax], TW, BY);
             for (int n = 0; n < m->nmech && ok; ++n) ok = encode_map<SP>(encode, &v.psi[n][ax], m, m->psi1[n][ax], TW, BY);
         }
+        // pressure sweep: v_x box with 4 columns either side, v_y box with
+        // 4 rows below and 3 above
+        constexpr int BP = Tile3<R>::BYP;
+        PresMaps &q = m->pres_maps;
+        ok = ok && encode_map<SS>(encode, &q.vz_own, m, m->v[2], TW, BP) &&
+             encode_map<SS>(encode, &q.vx_halo, m, m->v[0], TW + 8, BP) &&
+             encode_map<SS>(encode, &q.vy_halo, m, m->v[1], TW, BP + 7) &&
+             encode_map<SS>(encode, &q.p_own, m, m->p, TW, BP) && encode_map<SS>(encode, &q.kdt, m, m->kdt, TW, BP) &&
+             encode_map<uint16_t>(encode, &q.cls, m, m->cls, TW, BP) &&
+             encode_map<SS>(encode, &q.rho_own, m, m->rho, TW, BP) &&
+             (!m->nonlinear || encode_map<SS>(encode, &q.b2dt, m, m->b2dt, TW, BP));
+        for (int n = 0; n < m->nmech && ok; ++n) ok = encode_map<SP>(encode, &q.psi[n], m, m->psi2[n], TW, BP);
         return ok;
     }
 }
@@ -111,6 +123,7 @@ cudaError_t launch_dn(const fw_medium *m, cudaStream_t s, int which)
     using LV = VelSmem<R, SS, SP, DIM, NM, BX, BYV, TS>;
     using LVT = VelSmem<R, SS, SP, DIM, NM, BX, BYV, TS, CAN_TMA>;
     using LP = PresSmem<R, SS, SP, DIM, NM, BX, BYP, TS>;
+    using LPT = PresSmem<R, SS, SP, DIM, NM, BX, BYP, TS, CAN_TMA>;
     if (which & 4) {
         cudaError_t e = cudaFuncSetAttribute(k_velocity<R, SS, SP, DIM, NM, BX, BYV, TS, false>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LV::bytes);
@@ -119,11 +132,19 @@ cudaError_t launch_dn(const fw_medium *m, cudaStream_t s, int which)
                 e = cudaFuncSetAttribute(k_velocity<R, SS, SP, DIM, NM, BX, BYV, TS, true>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LVT::bytes);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_pressure<R, SS, SP, DIM, NM, BX, BYP, true, TS>,
+            e = cudaFuncSetAttribute(k_pressure<R, SS, SP, DIM, NM, BX, BYP, true, TS, false>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LP::bytes);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_pressure<R, SS, SP, DIM, NM, BX, BYP, false, TS>,
+            e = cudaFuncSetAttribute(k_pressure<R, SS, SP, DIM, NM, BX, BYP, false, TS, false>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LP::bytes);
+        if constexpr (CAN_TMA) {
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_pressure<R, SS, SP, DIM, NM, BX, BYP, true, TS, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LPT::bytes);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_pressure<R, SS, SP, DIM, NM, BX, BYP, false, TS, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LPT::bytes);
+        }
         return e;
     }
     const Geo<R> g = make_geo<R>(m);
@@ -175,10 +196,20 @@ cudaError_t launch_dn(const fw_medium *m, cudaStream_t s, int which)
     pa.mon = m->mon;
     pa.rho = static_cast<const SS *>(m->rho);
     const dim3 gp(gx, (m->NY + BYP - 1) / BYP, gz), bp(BX, BYP);
+    if constexpr (CAN_TMA) {
+        if (m->tma) {
+            pa.maps = m->pres_maps;
+            if (m->nonlinear)
+                k_pressure<R, SS, SP, DIM, NM, BX, BYP, true, TS, true><<<gp, bp, LPT::bytes, s>>>(pa);
+            else
+                k_pressure<R, SS, SP, DIM, NM, BX, BYP, false, TS, true><<<gp, bp, LPT::bytes, s>>>(pa);
+            return cudaGetLastError();
+        }
+    }
     if (m->nonlinear)
-        k_pressure<R, SS, SP, DIM, NM, BX, BYP, true, TS><<<gp, bp, LP::bytes, s>>>(pa);
+        k_pressure<R, SS, SP, DIM, NM, BX, BYP, true, TS, false><<<gp, bp, LP::bytes, s>>>(pa);
     else
-        k_pressure<R, SS, SP, DIM, NM, BX, BYP, false, TS><<<gp, bp, LP::bytes, s>>>(pa);
+        k_pressure<R, SS, SP, DIM, NM, BX, BYP, false, TS, false><<<gp, bp, LP::bytes, s>>>(pa);
     return cudaGetLastError();
 }
 
