@@ -12,10 +12,12 @@ Geometry, source, receiver, reference domain, relaxation sets and the
 stability rule are those of tests/test_gpu_pml_reflection.py (Sec. 4.3
 protocol, the oracle's stored fits at the paper's settings).  Run:
 
-    python tests/pml_readings_cpu.py [n_pairs]
+    python tests/pml_readings_cpu.py [n_pairs] [R0] [configs]
 
 It prints, per reading and layer configuration, the median reflection, the
 share below -50 dB and the unstable runs beside the paper's Sec. 5.5 figures.
+R0 (default 1e-5) is the design reflection of the absorbing profile;
+configs a comma list of adaptive, hom_T, hom_noT (default all three).
 """
 import math
 import os
@@ -36,13 +38,16 @@ import test_gpu_pml_reflection as proto  # noqa: E402
 PAPER = {"adaptive": (-58.5, 97.1, 0), "hom_T": (-54.5, 85.1, 0), "hom_noT": (-41.9, 1.1, 29)}
 
 
+R0 = 1e-5
+
+
 def trace(params, cfg, extra, ramp, tail=0):
     """Receiver trace of one oracle run; with tail > 0 also whether the run
     stays finite and below the pulse's peak for tail more steps."""
     shape, cls, src, rcv, lt = proto._geometry(cfg, extra)
     med = OracleMedium(shape, proto.DX, proto.DT, np.full(shape, proto.C0), np.full(shape, proto.RHO), cls, params,
                        pml=proto.LB, transition=lt, f0=proto.F0, layer_relax=cfg != "adaptive",
-                       tissue_ramp_on=ramp)
+                       tissue_ramp_on=ramp, R0=R0)
     sim = OracleSim(med)
     sim.set_sources(src, proto._wave()[None])
     sim.set_receivers(rcv, proto.NT)
@@ -58,15 +63,15 @@ def trace(params, cfg, extra, ramp, tail=0):
     return tr, stable
 
 
-def sweep(n_pairs=None):
+def sweep(n_pairs=None, configs=proto.CONFIGS, readings=(True, False)):
     design = stored_set(0.5, 1.0)[0]
     pairs = [(a, y) for y in proto.YS for a in proto.ALPHA0]
     pairs = [p for p in pairs if not stored_set(*p)[1]["failed"]]
     if n_pairs:
         pairs = pairs[::max(1, len(pairs) // n_pairs)][:n_pairs]
     out = {}
-    for ramp in (True, False):
-        for cfg in proto.CONFIGS:
+    for ramp in readings:
+        for cfg in configs:
             refl, bad = [], 0
             for pair in pairs:
                 params = [stored_set(*pair)[0], design]
@@ -85,4 +90,10 @@ def sweep(n_pairs=None):
 
 
 if __name__ == "__main__":
-    sweep(int(sys.argv[1]) if len(sys.argv) > 1 else None)
+    if len(sys.argv) > 2:
+        R0 = float(sys.argv[2])
+    cfgs = tuple(sys.argv[3].split(",")) if len(sys.argv) > 3 else proto.CONFIGS
+    print("design reflection R0 = %g" % R0, flush=True)
+    # with a design reflection given: the library's reading (ramped) only
+    sweep(int(sys.argv[1]) if len(sys.argv) > 1 and sys.argv[1] else None, cfgs,
+          (True,) if len(sys.argv) > 2 else (True, False))
