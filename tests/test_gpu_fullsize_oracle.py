@@ -6,14 +6,14 @@ traces, at several times in the run (errors scaled by the largest norm the
 field reached, as in the parity tests).
 
 These runs tie the FP32 full-size comparisons (FP32 kernels against the FP64
-kernels, tests/test_gpu_fullsize.py) to the oracle.  The bound is the
-rounding floor of the problem itself, measured in the same test: the oracle
-is run a second time with every K dt and every dt/rho_face moved up by one
-ulp, and the GPU may differ from the oracle by at most 4 times what that
-perturbation moves the oracle (a one-ulp change of the coefficients is the
-size of the difference between two correct FP64 evaluations of them in a
-different order), and in no case by more than 1e-9.  Both numbers are
-printed."""
+kernels, tests/test_gpu_fullsize.py) to the oracle.  Bound: 1e-11, the FP64
+target.  For the record of the rounding floor the Voronoi test also runs
+the oracle a second time with every K dt and every dt/rho_face moved up by
+one ulp (the size of the difference between two correct FP64 evaluations
+of them in a different order) and requires the GPU to stay within 4 times
+what that perturbation moves the oracle; both numbers are printed.  (The
+two-layer run skips the second oracle run: it would double the test's
+time.)"""
 import numpy as np
 import pytest
 
@@ -24,7 +24,7 @@ from synthetic import config_c2, config_c5
 
 pytestmark = pytest.mark.gpu
 
-CAP = 1e-9
+BOUND = 1e-11
 FACTOR = 4.0
 
 
@@ -58,8 +58,8 @@ def _fields(get_p, get_v, nd):
     return out
 
 
-def _compare(fw, spec, params, cls, beta=None, checks=3):
-    """(GPU FP64 vs oracle, bumped oracle vs oracle) per field."""
+def _compare(fw, spec, params, cls, beta=None, checks=3, perturbed=True):
+    """(GPU FP64 vs oracle, bumped oracle vs oracle or None) per field."""
     nd = len(spec.shape)
     gpu = fw.Medium.from_classes(spec.shape, spec.dx, spec.maps["c"], spec.maps["rho"], cls.astype(np.uint16),
                                  [to_c(p, fw) for p in params], dt=spec.dt, beta=beta, pml=spec.pml,
@@ -67,25 +67,30 @@ def _compare(fw, spec, params, cls, beta=None, checks=3):
     gpu.set_sources(spec.src_mask, spec.src_waves, spec.src_wave_of)
     gpu.set_receivers(spec.rcv_mask, spec.n_steps)
     ref = _oracle(spec, params, cls, beta, False)
-    bumped = _oracle(spec, params, cls, beta, True)
+    bumped = _oracle(spec, params, cls, beta, True) if perturbed else None
     err = {"gpu": {}, "ulp": {}}
     scale = {}
     bounds = np.linspace(0, spec.n_steps, checks + 1).round().astype(int)
     for a, b in zip(bounds[:-1], bounds[1:]):
         gpu.run(int(b - a))
         ref.run(int(b - a))
-        bumped.run(int(b - a))
+        if bumped:
+            bumped.run(int(b - a))
         r = _fields(lambda: ref.p, lambda d: ref.v[d], nd)
         g = _fields(lambda: gpu.read_field(0, 0, f64=True), lambda d: gpu.read_field(1, d, f64=True), nd)
-        u = _fields(lambda: bumped.p, lambda d: bumped.v[d], nd)
         for k in r:
             key = "v" if k.startswith("v") else k
             scale[key] = max(scale.get(key, 0.0), float(np.linalg.norm(r[k])))
             err["gpu"][k] = max(err["gpu"].get(k, 0.0), float(np.linalg.norm(g[k] - r[k])))
-            err["ulp"][k] = max(err["ulp"].get(k, 0.0), float(np.linalg.norm(u[k] - r[k])))
+            if bumped:
+                u = bumped.p if k == "p" else bumped.v[int(k[1:])]
+                err["ulp"][k] = max(err["ulp"].get(k, 0.0), float(np.linalg.norm(u - r[k])))
     out = {w: {k: e / scale["v" if k.startswith("v") else k] for k, e in err[w].items()} for w in err}
     out["gpu"]["traces"] = rel_l2(gpu.receivers(f64=True), ref.traces)
-    out["ulp"]["traces"] = rel_l2(bumped.traces, ref.traces)
+    if bumped:
+        out["ulp"]["traces"] = rel_l2(bumped.traces, ref.traces)
+    else:
+        out["ulp"] = None
     rc, _ = gpu.status()
     assert rc == 0
     gpu.close()
@@ -94,10 +99,12 @@ def _compare(fw, spec, params, cls, beta=None, checks=3):
 
 def _check(name, res):
     print("\n%s FP64 kernels vs FP64 oracle: %s" % (name, {k: "%.2e" % v for k, v in res["gpu"].items()}))
-    print("%s one-ulp perturbation of the oracle: %s" % (name, {k: "%.2e" % v for k, v in res["ulp"].items()}))
+    if res["ulp"] is not None:
+        print("%s one-ulp perturbation of the oracle: %s" % (name, {k: "%.2e" % v for k, v in res["ulp"].items()}))
     for k, v in res["gpu"].items():
-        bound = min(CAP, max(1e-11, FACTOR * res["ulp"][k]))
-        assert v <= bound, (k, v, bound)
+        assert v <= BOUND, (k, v)
+        if res["ulp"] is not None:
+            assert v <= FACTOR * res["ulp"][k], (k, v, res["ulp"][k])
 
 
 def test_c5_voronoi_1024_3000_steps_fp64_vs_oracle(fw):
@@ -112,4 +119,5 @@ def test_c2_two_layer_2048_5000_steps_fp64_vs_oracle(fw):
     params = [oracle_params(la["alpha0"], la["y"], 4), oracle_params(lb["alpha0"], lb["y"], 4)]
     n = spec.shape[0]
     cls = (np.arange(n)[:, None] >= spec.extra["interface"]).astype(np.uint16) * np.ones(spec.shape, np.uint16)
-    _check("2048^2 two-layer nonlinear, 5000 steps", _compare(fw, spec, params, cls, beta=spec.maps["beta"]))
+    _check("2048^2 two-layer nonlinear, 5000 steps",
+           _compare(fw, spec, params, cls, beta=spec.maps["beta"], perturbed=False))
