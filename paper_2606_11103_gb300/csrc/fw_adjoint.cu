@@ -26,9 +26,7 @@
 // One reverse step is five launches: receiver injection, source-gain
 // gradient, pressure adjoint (pointwise, writes the adjoint of q_d), velocity
 // adjoint (stencil of that, pointwise, writes the adjoint of g_d), and the
-// stencil update of the pressure adjoint.  The three adjoint kernels march
-// the depth axis per (x, y) column with register queues for the depth taps.
-// Gradients accumulate in FP64.
+// stencil update of the pressure adjoint.  Gradients accumulate in FP64.
 // The linear system only (no nonlinear factor); FP32 and FP64 media.
 #include "fw_internal.h"
 #include "fw_kernels.cuh"
@@ -51,7 +49,6 @@ constexpr int kDStride = 16;   // derivative table per class: dA1[4], dB1[4], dA
 
 template <typename R> struct AdjArgs {
     int nx, ny, nz, px, nmech;
-    int zseg;          // depth planes each thread marches
     long long plane, vol;
     bool ax_on[3];
     R c1, c2, c3, c4, dt;
@@ -78,47 +75,20 @@ template <typename R> struct Pt {
     long long st[3];   // strides
 };
 
-// Each thread owns one (x, y) column: x from the block's x range and thread,
-// y from the grid's y, and marches a segment of the depth axis (the grid's z
-// indexes the segments).  The depth-direction stencil taps come from a
-// register queue of 8 planes (one new load per plane instead of eight
-// strided ones), the x and y taps from the caches.
+// One thread per point: x from the block's x range and thread, the other two
+// kernel axes from the grid's y and z (no division of a flat index).
 template <typename R>
-__device__ __forceinline__ bool column(const AdjArgs<R> &A, Pt<R> &p, long long &b, int &z0, int &z1)
+__device__ __forceinline__ bool point(const AdjArgs<R> &A, Pt<R> &p, long long &i)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= A.nx) return false;
     p.c[0] = x;
     p.c[1] = blockIdx.y;
+    p.c[2] = blockIdx.z;
     p.n[0] = A.nx; p.n[1] = A.ny; p.n[2] = A.nz;
     p.st[0] = 1; p.st[1] = A.px; p.st[2] = A.plane;
-    b = (long long)blockIdx.y * A.px + x;
-    z0 = blockIdx.z * A.zseg;
-    z1 = min(A.nz, z0 + A.zseg);
+    i = (long long)blockIdx.z * A.plane + (long long)blockIdx.y * A.px + x;
     return true;
-}
-
-// value of f at depth kk of the column b, zero outside the grid
-template <typename R>
-__device__ __forceinline__ R zat(const AdjArgs<R> &A, const R *f, long long b, int kk)
-{
-    return (kk >= 0 && kk < A.nz) ? f[(long long)kk * A.plane + b] : R(0);
-}
-
-// a depth-axis staggered derivative from a queue of 8 planes: with
-// q[j] = f at k - 4 + j it is D- at k, with q[j] = f at k - 3 + j it is D+
-// at k + 1/2 (the same terms in the same order as dminus / dplus)
-template <typename R>
-__device__ __forceinline__ R qdiff(const AdjArgs<R> &A, const R (&q)[8])
-{
-    return A.c1 * (q[4] - q[3]) + A.c2 * (q[5] - q[2]) + A.c3 * (q[6] - q[1]) + A.c4 * (q[7] - q[0]);
-}
-
-template <typename R>
-__device__ __forceinline__ void qshift(R (&q)[8])
-{
-#pragma unroll
-    for (int j = 0; j < 7; ++j) q[j] = q[j + 1];
 }
 
 // forward staggered derivative at c + 1/2: sum_m c_m (f[c+m] - f[c-m+1])
@@ -153,23 +123,16 @@ template <typename R, int DIM, int NM>
 __global__ void k_adj_pres(const AdjArgs<R> A)
 {
     Pt<R> P;
-    long long b;
-    int z0, z1;
-    if (!column(A, P, b, z0, z1)) return;
-    R vz[8];     // v_z after the step at depths k-4 .. k+3
-#pragma unroll
-    for (int j = 0; j < 7; ++j) vz[j] = zat(A, A.fv1[2], b, z0 - 4 + j);
-    for (int k = z0; k < z1; ++k) {
-        vz[7] = zat(A, A.fv1[2], b, k + 3);
-        P.c[2] = k;
-        const long long i = (long long)k * A.plane + b;
+    long long i;
+    if (!point(A, P, i)) return;
+    {
         const R *t = A.lut + (size_t)A.cls[i] * kLutStride;
         const R *dtb = A.dlut + (size_t)A.cls[i] * kDStride;
         R q[3] = {0, 0, 0}, div = 0;
 #pragma unroll
         for (int ax = 0; ax < 3; ++ax)
             if (DIM == 3 || ax != 1) {
-                q[ax] = ax == 2 ? qdiff(A, vz) : dminus(A, A.fv1[ax], i, P.c[ax], P.n[ax], P.st[ax]);
+                q[ax] = dminus(A, A.fv1[ax], i, P.c[ax], P.n[ax], P.st[ax]);
                 div += q[ax];
             }
         const R lp = A.lp[i];
@@ -211,7 +174,6 @@ __global__ void k_adj_pres(const AdjArgs<R> A)
         }
         A.gk[i] += double(-stp * lp);
         A.gs[i] += double(gs);
-        qshift(vz);
     }
 }
 
@@ -219,20 +181,9 @@ template <typename R, int DIM, int NM>
 __global__ void k_adj_vel(const AdjArgs<R> A)
 {
     Pt<R> P;
-    long long b;
-    int z0, z1;
-    if (!column(A, P, b, z0, z1)) return;
-    R qq[8], pp[8];   // adjoint of q_z and forward p at depths k-3 .. k+4
-#pragma unroll
-    for (int j = 0; j < 7; ++j) {
-        qq[j] = zat(A, A.Q[2], b, z0 - 3 + j);
-        pp[j] = zat(A, A.fp, b, z0 - 3 + j);
-    }
-    for (int k = z0; k < z1; ++k) {
-        qq[7] = zat(A, A.Q[2], b, k + 4);
-        pp[7] = zat(A, A.fp, b, k + 4);
-        P.c[2] = k;
-        const long long i = (long long)k * A.plane + b;
+    long long i;
+    if (!point(A, P, i)) return;
+    {
         const R *t = A.lut + (size_t)A.cls[i] * kLutStride;
         const R *dtb = A.dlut + (size_t)A.cls[i] * kDStride;
         const R own = A.rho[i];
@@ -244,11 +195,11 @@ __global__ void k_adj_vel(const AdjArgs<R> A)
             if (DIM == 2 && ax == 1) continue;
             const int c = P.c[ax], n = P.n[ax];
             const long long st = P.st[ax];
-            const R lv = A.lv[ax][i] - (ax == 2 ? qdiff(A, qq) : dplus(A, A.Q[ax], i, c, n, st));
+            const R lv = A.lv[ax][i] - dplus(A, A.Q[ax], i, c, n, st);
             const R nxt = (c + 1 < n) ? A.rho[i + st] : own;
             const R dtr = R(2) * A.dt * fw_rcp(own + nxt);
             const R lst = -dtr * lv;
-            const R g = ax == 2 ? qdiff(A, pp) : dplus(A, A.fp, i, c, n, st);
+            const R g = dplus(A, A.fp, i, c, n, st);
             R lg = ce * lst;
 #pragma unroll
             for (int m = 0; m < NM; ++m) {
@@ -272,8 +223,6 @@ __global__ void k_adj_vel(const AdjArgs<R> A)
             A.lv[ax][i] = lv;
         }
         A.gs[i] += double(gs);
-        qshift(qq);
-        qshift(pp);
     }
 }
 
@@ -281,22 +230,14 @@ template <typename R, int DIM, int NM>
 __global__ void k_adj_p(const AdjArgs<R> A)
 {
     Pt<R> P;
-    long long b;
-    int z0, z1;
-    if (!column(A, P, b, z0, z1)) return;
-    R gz[8];     // adjoint of g_z at depths k-4 .. k+3
-#pragma unroll
-    for (int j = 0; j < 7; ++j) gz[j] = zat(A, A.Gd[2], b, z0 - 4 + j);
-    for (int k = z0; k < z1; ++k) {
-        gz[7] = zat(A, A.Gd[2], b, k + 3);
-        P.c[2] = k;
-        const long long i = (long long)k * A.plane + b;
+    long long i;
+    if (!point(A, P, i)) return;
+    {
         R s = 0;
 #pragma unroll
         for (int ax = 0; ax < 3; ++ax)
-            if (DIM == 3 || ax != 1) s += ax == 2 ? qdiff(A, gz) : dminus(A, A.Gd[ax], i, P.c[ax], P.n[ax], P.st[ax]);
+            if (DIM == 3 || ax != 1) s += dminus(A, A.Gd[ax], i, P.c[ax], P.n[ax], P.st[ax]);
         A.lp[i] -= s;
-        qshift(gz);
     }
 }
 
@@ -362,29 +303,29 @@ __global__ void k_grad_out(const double *uc, const double *us, const float *a0f,
 // the three adjoint kernels of one reverse step, instantiated per dimension
 // and number of mechanisms (their loops unroll)
 template <typename R, int DIM, int NM>
-void launch_reverse_dn(const AdjArgs<R> &A, dim3 grid, int threads, cudaStream_t s)
+void launch_reverse_dn(const AdjArgs<R> &A, dim3 grid, cudaStream_t s)
 {
-    k_adj_pres<R, DIM, NM><<<grid, threads, 0, s>>>(A);
-    k_adj_vel<R, DIM, NM><<<grid, threads, 0, s>>>(A);
-    k_adj_p<R, DIM, NM><<<grid, threads, 0, s>>>(A);
+    k_adj_pres<R, DIM, NM><<<grid, 256, 0, s>>>(A);
+    k_adj_vel<R, DIM, NM><<<grid, 256, 0, s>>>(A);
+    k_adj_p<R, DIM, NM><<<grid, 256, 0, s>>>(A);
 }
 
 template <typename R>
-void launch_reverse(const AdjArgs<R> &A, int ndim, int nmech, dim3 grid, int threads, cudaStream_t s)
+void launch_reverse(const AdjArgs<R> &A, int ndim, int nmech, dim3 grid, cudaStream_t s)
 {
     if (ndim == 2) {
         switch (nmech) {
-        case 1: launch_reverse_dn<R, 2, 1>(A, grid, threads, s); break;
-        case 2: launch_reverse_dn<R, 2, 2>(A, grid, threads, s); break;
-        case 3: launch_reverse_dn<R, 2, 3>(A, grid, threads, s); break;
-        default: launch_reverse_dn<R, 2, 4>(A, grid, threads, s); break;
+        case 1: launch_reverse_dn<R, 2, 1>(A, grid, s); break;
+        case 2: launch_reverse_dn<R, 2, 2>(A, grid, s); break;
+        case 3: launch_reverse_dn<R, 2, 3>(A, grid, s); break;
+        default: launch_reverse_dn<R, 2, 4>(A, grid, s); break;
         }
     } else {
         switch (nmech) {
-        case 1: launch_reverse_dn<R, 3, 1>(A, grid, threads, s); break;
-        case 2: launch_reverse_dn<R, 3, 2>(A, grid, threads, s); break;
-        case 3: launch_reverse_dn<R, 3, 3>(A, grid, threads, s); break;
-        default: launch_reverse_dn<R, 3, 4>(A, grid, threads, s); break;
+        case 1: launch_reverse_dn<R, 3, 1>(A, grid, s); break;
+        case 2: launch_reverse_dn<R, 3, 2>(A, grid, s); break;
+        case 3: launch_reverse_dn<R, 3, 3>(A, grid, s); break;
+        default: launch_reverse_dn<R, 3, 4>(A, grid, s); break;
         }
     }
 }
@@ -524,14 +465,7 @@ int gradient_impl(fw_medium *m, int n_steps, int K, const void *G, const void *a
     A.gk = static_cast<double *>(gacc.p);
     A.gs = static_cast<double *>(gacc.p) + vol;
     auto image = [&](int k) { return static_cast<const char *>(seg.p) + (size_t)k * SB; };
-    // one thread per (x, y) column marching a depth segment: 64-thread blocks,
-    // segments of 8..64 planes such that the grid has at least 8 blocks per SM
-    const int threads = 64;
-    const long long cols = (long long)((m->NX + threads - 1) / threads) * m->NY;
-    int zseg = 64;
-    while (zseg > 8 && cols * ((m->NZ + zseg - 1) / zseg) < 152LL * 8) zseg /= 2;
-    A.zseg = zseg;
-    const dim3 pgrid((unsigned)((m->NX + threads - 1) / threads), (unsigned)m->NY, (unsigned)((m->NZ + zseg - 1) / zseg));
+    const dim3 pgrid((unsigned)((m->NX + 255) / 256), (unsigned)m->NY, (unsigned)m->NZ);   // one thread per point
     const double inv_dxd = 1.0 / std::pow(m->dx, m->ndim);
 
     // ---- reverse sweep, one checkpoint segment at a time ----
@@ -564,7 +498,7 @@ int gradient_impl(fw_medium *m, int n_steps, int K, const void *G, const void *a
                     A.fpsi1[q][ax] = m->psi1[q][ax] ? reinterpret_cast<const R *>(F + off(m->psi1[q][ax])) : nullptr;
             }
             for (int q = 0; q < m->nmech; ++q) A.fpsi2[q] = reinterpret_cast<const R *>(F + off(m->psi2[q]));
-            launch_reverse<R>(A, m->ndim, m->nmech, pgrid, threads, s);
+            launch_reverse<R>(A, m->ndim, m->nmech, pgrid, s);
         }
         ADJ_CK(cudaGetLastError());
     }

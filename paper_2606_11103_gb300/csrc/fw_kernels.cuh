@@ -376,12 +376,11 @@ struct VelSmem {
     static constexpr size_t sr_stride = ((size_t)(BY + 1) * (TW + 4) * sizeof(R) + 127) / 128 * 128;
     static constexpr size_t o_sp = 2 * stage;
     static constexpr size_t o_sr = o_sp + 2 * sp_stride;
-    // two mbarriers and two release counters (TMA staging) in the padding
-    // after the second rho tile, which its copies do not reach: the layout's
-    // size is that of the cp.async variant, so both fit the same number of
-    // CTAs per SM
+    // two mbarriers (TMA staging) in the padding after the second rho tile,
+    // which its copies do not reach: the layout's size is that of the
+    // cp.async variant, so both fit the same number of CTAs per SM
     static constexpr size_t o_bar = o_sr + sr_stride + ((size_t)(BY + 1) * (TW + 4) * sizeof(R) + 7) / 8 * 8;
-    static_assert(o_bar + 24 <= o_sr + 2 * sr_stride, "no room for the barriers in the rho tile padding");
+    static_assert(o_bar + 16 <= o_sr + 2 * sr_stride, "no room for the barriers in the rho tile padding");
     static constexpr size_t bytes = o_sr + 2 * sr_stride;
     // bytes the TMA copies of one plane deliver (completion count of its barrier)
     static constexpr unsigned tma_bytes =
@@ -407,8 +406,8 @@ struct PresSmem {
     static constexpr size_t svy_stride = ((size_t)SHY * TW * sizeof(R) + 127) / 128 * 128;
     static constexpr size_t o_svx = 2 * stage;
     static constexpr size_t o_svy = o_svx + 2 * svx_stride;
-    static constexpr size_t o_bar = o_svy + 2 * svy_stride;                 // two mbarriers, two counters (TMA)
-    static constexpr size_t bytes = o_bar + (TMA ? 24 : 0);
+    static constexpr size_t o_bar = o_svy + 2 * svy_stride;                 // two mbarriers (TMA staging)
+    static constexpr size_t bytes = o_bar + (TMA ? 16 : 0);
 };
 
 // ---------------------------------------------------------------------------
@@ -441,28 +440,6 @@ __device__ __forceinline__ void vel_issue_tma(const VelArgs<R, SS, SP> &A, unsig
     tma_load_3d(sm + L::o_sr + (k & 1) * L::sr_stride, &A.maps.rho_halo, xb, yb, k, bar);
 }
 
-// TMA staging without CTA barriers: a warp that is done reading the stage
-// and tiles of plane k releases them; the last warp of the CTA to do so
-// refills them with plane k+2.  The fence and the warp barrier complete the
-// warp's shared-memory reads before its release; the refill orders them
-// before the copies (fence.proxy.async in the issue).  cnt[2]: releases of
-// the buffers of parity 0 and 1.
-template <int NT, typename Issue>
-__device__ __forceinline__ void release_and_refill(unsigned *cnt, int k, Issue &&issue)
-{
-    constexpr unsigned NW = NT / 32;
-    static_assert(NT % 32 == 0, "whole warps");
-    __threadfence_block();
-    __syncwarp();
-    if ((threadIdx.x + threadIdx.y * blockDim.x) % 32 == 0) {
-        const unsigned old = atomicAdd(cnt + (k & 1), 1u);
-        if (old == NW - 1) {
-            cnt[k & 1] = 0;
-            issue();
-        }
-    }
-}
-
 template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY, bool TS, bool TMA>
 __device__ __forceinline__ void vel_issue(const VelArgs<R, SS, SP> &A, unsigned char *sm, int k, int x0, int y,
                                           int xb, int yb, long long row, bool hd)
@@ -474,7 +451,7 @@ __device__ __forceinline__ void vel_issue(const VelArgs<R, SS, SP> &A, unsigned 
     unsigned char *st = sm + (k & 1) * L::stage;
     const int e0 = ty * L::TW + 4 * tx;       // this thread's element offset in a stage tile
     if (TMA) {
-        // the tile copies are issued by vel_issue_tma (prologue, vel_release);
+        if (tx == 0 && ty == 0) vel_issue_tma<R, SS, SP, NM, BX, BY, TS>(A, sm, k, xb, yb);
         // absorbing-layer memory: per thread, where this thread needs it
         if (G.wabs > 0 && hd) {
             const bool in[3] = {x0 < G.wabs || x0 + 3 >= G.nx - G.wabs, y < G.wabs || y >= G.ny - G.wabs,
@@ -682,18 +659,13 @@ k_velocity(const __grid_constant__ VelArgs<R, SS, SP> A)
     }
     ld4_or_zero(A.rho + z0 * G.plane + row, hd && z0 < G.nz, rq[0]);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L::o_bar);
-    unsigned *cnt = reinterpret_cast<unsigned *>(smem + L::o_bar + 16);
     if (TMA) {
         if (tx == 0 && ty == 0) {
             mbar_init(bars, 1);
             mbar_init(bars + 1, 1);
-            cnt[0] = cnt[1] = 0;
             mbar_fence_init();
         }
         __syncthreads();
-        // the first two planes; later ones are issued by vel_release
-        if (tx == 0 && ty == 0)
-            for (int kk = z0; kk < min(z1, z0 + 2); ++kk) vel_issue_tma<R, SS, SP, NM, BX, BY, TS>(A, smem, kk, xb, yb);
     }
     bool timed_out = false;
     if (z0 < z1) vel_issue<R, SS, SP, DIM, NM, BX, BY, TS, TMA>(A, smem, z0, x0, y, xb, yb, row, hd);
@@ -726,7 +698,7 @@ k_velocity(const __grid_constant__ VelArgs<R, SS, SP> A)
         unsigned char *st = smem + buf * L::stage;
         R(*sp)[SW] = reinterpret_cast<R(*)[SW]>(smem + L::o_sp + buf * L::sp_stride);
         R(*sr)[TW + 4] = reinterpret_cast<R(*)[TW + 4]>(smem + L::o_sr + buf * L::sr_stride);
-        if (!TMA) __syncthreads();                 // iteration k-1 is done with stage/tiles (k+1)&1
+        __syncthreads();                           // iteration k-1 is done with stage/tiles (k+1)&1
         if (!TMA) {                                // centre of the tiles from registers (TMA copies them)
             R *dst = &sp[RO + ty][4 + 4 * tx];
             dst[0] = q[3][0]; dst[1] = q[3][1]; dst[2] = q[3][2]; dst[3] = q[3][3];
@@ -745,8 +717,7 @@ k_velocity(const __grid_constant__ VelArgs<R, SS, SP> A)
         if (TMA && !timed_out && !mbar_wait_bounded(bars + buf, (unsigned)((k - z0) >> 1) & 1u)) timed_out = true;
         // cp.async staging: everyone's copies and tile centres visible to all.
         // TMA staging: every thread has waited on the barrier itself and
-        // reads only its own cp.async copies (absorbing layer), so no barrier;
-        // buffers are refilled only after every warp released them
+        // reads only its own cp.async copies (absorbing layer), so no barrier
         if (!TMA) __syncthreads();
         Sm<SS>::ld(reinterpret_cast<const SS *>(st + L::o_pn) + e0, q[7]);
         Sm<SS>::ld(reinterpret_cast<const SS *>(st + L::o_rn) + e0, rq[1]);
@@ -873,10 +844,6 @@ k_velocity(const __grid_constant__ VelArgs<R, SS, SP> A)
                 if (pml_here) Io<SS>::st(A.psip[ax] + pk + row, pp);
             }
         }
-        if (TMA)      // done with the stage and tiles of plane k: refill them with plane k+2
-            release_and_refill<BX * BY>(cnt, k, [&] {
-                if (k + 2 < z1) vel_issue_tma<R, SS, SP, NM, BX, BY, TS>(A, smem, k + 2, xb, yb);
-            });
 #pragma unroll
         for (int j = 0; j < 7; ++j)
 #pragma unroll
@@ -933,7 +900,7 @@ __device__ __forceinline__ void pres_issue(const PresArgs<R, SS, SP> &A, unsigne
     unsigned char *st = sm + (k & 1) * L::stage;
     const int e0 = ty * L::TW + 4 * tx;
     if (TMA) {
-        // the tile copies are issued by pres_issue_tma (prologue, release);
+        if (tx == 0 && ty == 0) pres_issue_tma<R, SS, SP, NM, BX, BY, NL, TS>(A, sm, k, x0, yb);
         // absorbing-layer memory: per thread, where this thread needs it
         if (G.wabs > 0 && hd) {
             const bool in[3] = {x0 < G.wabs || x0 + 3 >= G.nx - G.wabs, y < G.wabs || y >= G.ny - G.wabs,
@@ -1127,18 +1094,13 @@ k_pressure(const __grid_constant__ PresArgs<R, SS, SP> A)
     R pmax = R(0);
     bool bad = false;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L::o_bar);
-    unsigned *cnt = reinterpret_cast<unsigned *>(smem + L::o_bar + 16);
     if (TMA) {
         if (tx == 0 && ty == 0) {
             mbar_init(bars, 1);
             mbar_init(bars + 1, 1);
-            cnt[0] = cnt[1] = 0;
             mbar_fence_init();
         }
         __syncthreads();
-        if (tx == 0 && ty == 0)
-            for (int kk = z0; kk < min(z1, z0 + 2); ++kk)
-                pres_issue_tma<R, SS, SP, NM, BX, BY, NL, TS>(A, smem, kk, xb, yb);
     }
     bool timed_out = false;
     if (z0 < z1) pres_issue<R, SS, SP, DIM, NM, BX, BY, NL, TS, TMA>(A, smem, z0, x0, y, yb, row, hd);
@@ -1166,7 +1128,7 @@ k_pressure(const __grid_constant__ PresArgs<R, SS, SP> A)
         unsigned char *st = smem + buf * L::stage;
         const R(*svx)[SWX] = reinterpret_cast<const R(*)[SWX]>(smem + L::o_svx + buf * L::svx_stride);
         const R(*svy)[TW] = reinterpret_cast<const R(*)[TW]>(smem + L::o_svy + buf * L::svy_stride);
-        if (!TMA) __syncthreads();                 // iteration k-1 is done with stage/tiles (k+1)&1
+        __syncthreads();
         if (k + 1 < z1) pres_issue<R, SS, SP, DIM, NM, BX, BY, NL, TS, TMA>(A, smem, k + 1, x0, y, yb, row, hd);
         cp_commit();
         const bool pml_z = G.wabs > 0 && (k < G.wabs || k >= G.nz - G.wabs);
@@ -1297,10 +1259,6 @@ k_pressure(const __grid_constant__ PresArgs<R, SS, SP> A)
                 if (pml_here) Io<SS>::st(A.psip[ax] + pk + row, pp[ax]);
             }
         }
-        if (TMA)      // done with the stage and tiles of plane k: refill them with plane k+2
-            release_and_refill<BX * BY>(cnt, k, [&] {
-                if (k + 2 < z1) pres_issue_tma<R, SS, SP, NM, BX, BY, NL, TS>(A, smem, k + 2, xb, yb);
-            });
 #pragma unroll
         for (int j = 0; j < 7; ++j)
 #pragma unroll
