@@ -11,7 +11,7 @@ velocity components share the largest component's norm):
 import numpy as np
 import pytest
 
-from gpu_util import Pair, oracle_params, rel_l2
+from gpu_util import Pair, oracle_params, rel_l2, to_c
 from synthetic import config_c1, config_c2, config_c3, config_c5, gaussian_pulse, voronoi_classes, voronoi_medium
 
 pytestmark = pytest.mark.gpu
@@ -226,3 +226,27 @@ def test_create_from_maps_fits_each_class(fw):
     m.run(10)
     assert m.status()[0] == 0
     m.close()
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_tma_staging_equals_cp_async_staging(fw, storage, monkeypatch):
+    """The 3D sweeps stage their streams by TMA; FWGB_NO_TMA=1 at medium
+    creation selects the per-thread cp.async staging instead.  Both feed the
+    same arithmetic, so the fields after 60 steps agree bitwise (ragged
+    crop: partial tiles in x and y, both halo edges)."""
+    box = ((0, 40), (230, 283), (221, 290))
+    spec = config_c3(n_steps=60, box=box)
+    params = [oracle_params(a, y, 4) for a, y in zip(spec.classes["alpha0"], spec.classes["y"])]
+    out = []
+    for no_tma in ("0", "1"):
+        monkeypatch.setenv("FWGB_NO_TMA", no_tma)
+        m = fw.Medium.from_classes(spec.shape, spec.dx, spec.maps["c"], spec.maps["rho"], spec.maps["class_idx"],
+                                   [to_c(p, fw) for p in params], dt=spec.dt, pml=8, f0=spec.f0, storage=storage)
+        m.set_sources(spec.src_mask, spec.src_waves, spec.src_wave_of)
+        m.run(60)
+        out.append([m.read_field(0, 0)] + [m.read_field(1, d) for d in range(3)] + [m.read_field(3, 1)])
+        assert m.status()[0] == 0
+        m.close()
+    assert np.abs(out[0][0]).max() > 0
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
