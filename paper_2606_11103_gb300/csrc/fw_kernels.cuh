@@ -788,20 +788,6 @@ k_velocity(const __grid_constant__ VelArgs<R, SS, SP> A)
                 }
                 pkey = cl;
             }
-            // class coefficients: when the four cells share one class (the
-            // common case) they are made current once here and the cell loops
-            // below run without class checks, so the compiler interleaves the
-            // four cells' recurrences; otherwise each cell checks its class
-            auto load_class = [&](int c) {
-                lut4(A.lut, c, 0, hdr);
-                lut4(A.lut, c, kLutA1, A1);
-                lut4(A.lut, c, kLutB1, B1);
-                lut4(A.lut, c, kLutH1, H1);
-                dk1 = __ldg(A.lut + (size_t)c * kLutStride + kLutDk);
-                ccls = c;
-            };
-            const bool uniform = cls4[0] == cls4[1] && cls4[1] == cls4[2] && cls4[2] == cls4[3];
-            if (uniform && cls4[0] != ccls) load_class(cls4[0]);
             // one direction at a time: its v and psi come from the stage
 #pragma unroll
             for (int ax = 0; ax < 3; ++ax) {
@@ -814,7 +800,17 @@ k_velocity(const __grid_constant__ VelArgs<R, SS, SP> A)
                 const bool pml_here = ax == 0 ? pml_x : (ax == 1 ? pml_y : pml_z);
                 R pp[4];
                 if (pml_here) Sm<SS>::ld(reinterpret_cast<const SS *>(st + L::o_pml) + ax * L::TILE + e0, pp);
-                auto cell = [&](int e) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int c = cls4[e];
+                    if (c != ccls) {
+                        lut4(A.lut, c, 0, hdr);
+                        lut4(A.lut, c, kLutA1, A1);
+                        lut4(A.lut, c, kLutB1, B1);
+                        lut4(A.lut, c, kLutH1, H1);
+                        dk1 = __ldg(A.lut + (size_t)c * kLutStride + kLutDk);
+                        ccls = c;
+                    }
                     // a dead lane (x >= nx) gets drive 0, so its memory variables stay exactly 0
                     const bool live = x0 + e < G.nx;
                     const R gd = live ? g[ax][e] : R(0);
@@ -841,16 +837,6 @@ k_velocity(const __grid_constant__ VelArgs<R, SS, SP> A)
                         }
                     }
                     vv[e] = live ? vv[e] - dtr[ax][e] * stv : R(0);
-                };
-                if (uniform) {
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) cell(e);
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        if (cls4[e] != ccls) load_class(cls4[e]);
-                        cell(e);
-                    }
                 }
                 Io<SS>::st(A.v[ax] + pk + row, vv);
 #pragma unroll
@@ -1216,19 +1202,17 @@ k_pressure(const __grid_constant__ PresArgs<R, SS, SP> A)
                 }
                 pkey = cl;
             }
-            // class coefficients: made current once when the four cells share
-            // one class, so the cell loop runs without class checks
-            auto load_class = [&](int c) {
-                lut4(A.lut, c, 0, hdr);
-                lut4(A.lut, c, kLutA2, A2);
-                lut4(A.lut, c, kLutB2, B2);
-                lut4(A.lut, c, kLutH2, H2);
-                dk2 = __ldg(A.lut + (size_t)c * kLutStride + kLutDk + 1);
-                ccls = c;
-            };
-            const bool uniform = cls4[0] == cls4[1] && cls4[1] == cls4[2] && cls4[2] == cls4[3];
-            if (uniform && cls4[0] != ccls) load_class(cls4[0]);
-            auto cell = [&](int e) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int c = cls4[e];
+                if (c != ccls) {
+                    lut4(A.lut, c, 0, hdr);
+                    lut4(A.lut, c, kLutA2, A2);
+                    lut4(A.lut, c, kLutB2, B2);
+                    lut4(A.lut, c, kLutH2, H2);
+                    dk2 = __ldg(A.lut + (size_t)c * kLutStride + kLutDk + 1);
+                    ccls = c;
+                }
                 const bool live = x0 + e < G.nx;
                 R div = qd[0][e] + qd[2][e];
                 if (DIM == 3) div += qd[1][e];
@@ -1265,16 +1249,6 @@ k_pressure(const __grid_constant__ PresArgs<R, SS, SP> A)
                 const R ap = fabs(pn);
                 bad |= !(ap <= R(3.0e38));
                 pmax = fmax(pmax, ap);
-            };
-            if (uniform) {
-#pragma unroll
-                for (int e = 0; e < 4; ++e) cell(e);
-            } else {
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    if (cls4[e] != ccls) load_class(cls4[e]);
-                    cell(e);
-                }
             }
             Io<SS>::st(A.p + pk + row, pv);
 #pragma unroll
