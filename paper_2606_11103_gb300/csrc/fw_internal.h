@@ -57,6 +57,7 @@ struct VelMaps {
 // rho (time-space stencil)
 struct PresMaps {
     TensorMapBlob vz_own, vx_halo, vy_halo, p_own, kdt, b2dt, psi[FW_MAX_MECH], cls, rho_own;
+    TensorMapBlob vx_ring, vy_ring, vz_ring;   // time-space stencil: v boxes with x and y halos
 };
 
 struct Graph {

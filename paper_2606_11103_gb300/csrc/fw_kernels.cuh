@@ -402,12 +402,24 @@ struct PresSmem {
     static constexpr size_t o_rh = o_pml + 3 * TILE * sizeof(SS);          // rho of plane k (time-space only)
     static constexpr size_t stage = (o_rh + (TS ? TILE * sizeof(SS) : 0) + 127) / 128 * 128;
     // v_x (x halo) and v_y (y halo) tiles, two each, on 128-byte boundaries
-    static constexpr size_t svx_stride = ((size_t)BY * SWX * sizeof(R) + 127) / 128 * 128;
-    static constexpr size_t svy_stride = ((size_t)SHY * TW * sizeof(R) + 127) / 128 * 128;
+    // (the time-space stencil with TMA staging uses the rings below instead)
+    static constexpr bool RINGS = TS && TMA;
+    static constexpr size_t svx_stride = RINGS ? 0 : ((size_t)BY * SWX * sizeof(R) + 127) / 128 * 128;
+    static constexpr size_t svy_stride = RINGS ? 0 : ((size_t)SHY * TW * sizeof(R) + 127) / 128 * 128;
     static constexpr size_t o_svx = 2 * stage;
     static constexpr size_t o_svy = o_svx + 2 * svx_stride;
-    static constexpr size_t o_bar = o_svy + 2 * svy_stride;                 // two mbarriers (TMA staging)
-    static constexpr size_t bytes = o_bar + (TMA ? 16 : 0);
+    // time-space stencil, TMA staging: rings of four planes (k-1, k, k+1 in
+    // use, k+2 landing) of v_x, v_y, v_z with x halos of 4 columns and y
+    // halos of 1 row (v_x, v_z: rows y-1 .. y+BY) or 4 below / 3 above (v_y)
+    static constexpr int RXH = BY + 2, RYH = BY + 7;
+    static constexpr size_t rx_stride = RINGS ? ((size_t)RXH * SWX * sizeof(R) + 127) / 128 * 128 : 0;
+    static constexpr size_t ry_stride = RINGS ? ((size_t)RYH * SWX * sizeof(R) + 127) / 128 * 128 : 0;
+    static constexpr size_t o_rx = o_svy + 2 * svy_stride;
+    static constexpr size_t o_ry = o_rx + 4 * rx_stride;
+    static constexpr size_t o_rz = o_ry + 4 * ry_stride;
+    static constexpr unsigned ring_bytes = (unsigned)(((size_t)2 * RXH + RYH) * SWX * sizeof(SS));
+    static constexpr size_t o_bar = o_rz + 4 * rx_stride;                   // mbarriers (TMA staging)
+    static constexpr size_t bytes = o_bar + (TMA ? (RINGS ? 48 : 16) : 0);
 };
 
 // ---------------------------------------------------------------------------
@@ -870,7 +882,7 @@ template <typename R, typename SS, typename SP, int NM, int BX, int BY, bool NL,
 __device__ __forceinline__ void pres_issue_tma(const PresArgs<R, SS, SP> &A, unsigned char *sm, int k, int xb, int yb)
 {
     using L = PresSmem<R, SS, SP, 3, NM, BX, BY, TS, true>;
-    constexpr unsigned bytes = (unsigned)(((size_t)BY * L::SWX + (size_t)L::SHY * L::TW) * sizeof(SS) +
+    constexpr unsigned bytes = (unsigned)((L::RINGS ? 0 : ((size_t)BY * L::SWX + (size_t)L::SHY * L::TW) * sizeof(SS)) +
                                           L::TILE * (3 + (NL ? 1 : 0) + (TS ? 1 : 0)) * sizeof(SS) +
                                           (size_t)NM * L::TILE * sizeof(SP) + L::TILE * 2);
     unsigned char *st = sm + (k & 1) * L::stage;
@@ -885,8 +897,77 @@ __device__ __forceinline__ void pres_issue_tma(const PresArgs<R, SS, SP> &A, uns
 #pragma unroll
     for (int m = 0; m < NM; ++m) tma_load_3d(st + L::o_psi + m * L::TILE * sizeof(SP), &A.maps.psi[m], xb, yb, k, bar);
     tma_load_3d(st + L::o_cls, &A.maps.cls, xb, yb, k, bar);
-    tma_load_3d(sm + L::o_svx + (k & 1) * L::svx_stride, &A.maps.vx_halo, xb - 4, yb, k, bar);
-    tma_load_3d(sm + L::o_svy + (k & 1) * L::svy_stride, &A.maps.vy_halo, xb, yb - 4, k, bar);
+    if (!L::RINGS) {
+        tma_load_3d(sm + L::o_svx + (k & 1) * L::svx_stride, &A.maps.vx_halo, xb - 4, yb, k, bar);
+        tma_load_3d(sm + L::o_svy + (k & 1) * L::svy_stride, &A.maps.vy_halo, xb, yb - 4, k, bar);
+    }
+}
+
+// Time-space stencil with TMA staging: plane k of the v rings (slot k&3,
+// barrier 2 + (k&3)); planes outside the grid read as zero
+template <typename R, typename SS, typename SP, int NM, int BX, int BY>
+__device__ __forceinline__ void pres_issue_rings(const PresArgs<R, SS, SP> &A, unsigned char *sm, int k, int xb, int yb)
+{
+    using L = PresSmem<R, SS, SP, 3, NM, BX, BY, true, true>;
+    const int s = k & 3;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + L::o_bar) + 2 + s;
+    fence_proxy_async_smem();
+    mbar_expect_tx(bar, L::ring_bytes);
+    tma_load_3d(sm + L::o_rx + s * L::rx_stride, &A.maps.vx_ring, xb - 4, yb - 1, k, bar);
+    tma_load_3d(sm + L::o_ry + s * L::ry_stride, &A.maps.vy_ring, xb - 4, yb - 4, k, bar);
+    tma_load_3d(sm + L::o_rz + s * L::rx_stride, &A.maps.vz_ring, xb - 4, yb - 1, k, bar);
+}
+
+// q_d = D-_d v_d with the time-space stencil from the rings (see
+// pres_divergence_ts for the stencil): ring slots of planes k-1, k, k+1 hold
+// v_x and v_z with rows y-1 .. y+BY and v_y with rows y-4 .. y+BY+2, all
+// with 4 columns of x halo; the depth taps of v_z come from the register
+// queue qz (planes k-4 .. k+3)
+template <typename R, typename SS, typename SP, int NM, int BX, int BY>
+__device__ __forceinline__ void pres_divergence_ts_rings(const PresArgs<R, SS, SP> &A, const unsigned char *st,
+                                                         const unsigned char *sm, const R (&qz)[8][4], const R (&kd)[4],
+                                                         int k, int x0, int e0, R (&qd)[3][4])
+{
+    using L = PresSmem<R, SS, SP, 3, NM, BX, BY, true, true>;
+    constexpr int SW = L::SWX;
+    const Geo<R> &G = A.g;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    auto rx = [&](int kk) { return reinterpret_cast<const R *>(sm + L::o_rx + (kk & 3) * L::rx_stride); };
+    auto ry = [&](int kk) { return reinterpret_cast<const R *>(sm + L::o_ry + (kk & 3) * L::ry_stride); };
+    auto rz = [&](int kk) { return reinterpret_cast<const R *>(sm + L::o_rz + (kk & 3) * L::rx_stride); };
+    const R *xk = rx(k), *xm = rx(k - 1), *xp = rx(k + 1);
+    const R *yk = ry(k), *ym = ry(k - 1), *yp = ry(k + 1);
+    const R *zk = rz(k), *zm = rz(k - 1);
+    R rh[4];
+    Sm<SS>::ld(reinterpret_cast<const SS *>(st + L::o_rh) + e0, rh);
+    const int c0 = 4 + 4 * tx;                     // column of x0 in the ring tiles
+    const int rX = ty + 1, rY = ty + 4;            // row of y in the v_x / v_z and in the v_y tiles
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int c = c0 + e;
+        const bool live = x0 + e < G.nx;
+        const R r2 = live ? kd[e] * G.r2s * fw_rcp(rh[e]) : R(0);
+        R a[4], b;
+        ts_weights(G, r2, a, b);
+        // v_x: x-derivative at x (v_x(i) - v_x(i-1) pairs), cross terms at y -+ 1 and planes k -+ 1
+        const R *w = xk + rX * SW;
+        const R Xx = (xk[(rX - 1) * SW + c] - xk[(rX - 1) * SW + c - 1]) + (xk[(rX + 1) * SW + c] - xk[(rX + 1) * SW + c - 1]) +
+                     (xm[rX * SW + c] - xm[rX * SW + c - 1]) + (xp[rX * SW + c] - xp[rX * SW + c - 1]);
+        qd[0][e] = a[0] * (w[c] - w[c - 1]) + a[1] * (w[c + 1] - w[c - 2]) + a[2] * (w[c + 2] - w[c - 3]) +
+                   a[3] * (w[c + 3] - w[c - 4]) + b * Xx;
+        // v_y: y-derivative at y (v_y(j) - v_y(j-1)), cross terms at x -+ 1 and planes k -+ 1
+        const R *v = yk + c;
+        const R Xy = (yk[rY * SW + c - 1] - yk[(rY - 1) * SW + c - 1]) + (yk[rY * SW + c + 1] - yk[(rY - 1) * SW + c + 1]) +
+                     (ym[rY * SW + c] - ym[(rY - 1) * SW + c]) + (yp[rY * SW + c] - yp[(rY - 1) * SW + c]);
+        qd[1][e] = a[0] * (v[rY * SW] - v[(rY - 1) * SW]) + a[1] * (v[(rY + 1) * SW] - v[(rY - 2) * SW]) +
+                   a[2] * (v[(rY + 2) * SW] - v[(rY - 3) * SW]) + a[3] * (v[(rY + 3) * SW] - v[(rY - 4) * SW]) +
+                   b * Xy;
+        // v_z: depth derivative from the queue, cross terms at x -+ 1 and y -+ 1 (planes k, k-1)
+        const R Xz = (zk[rX * SW + c - 1] - zm[rX * SW + c - 1]) + (zk[rX * SW + c + 1] - zm[rX * SW + c + 1]) +
+                     (zk[(rX - 1) * SW + c] - zm[(rX - 1) * SW + c]) + (zk[(rX + 1) * SW + c] - zm[(rX + 1) * SW + c]);
+        qd[2][e] = a[0] * (qz[4][e] - qz[3][e]) + a[1] * (qz[5][e] - qz[2][e]) + a[2] * (qz[6][e] - qz[1][e]) +
+                   a[3] * (qz[7][e] - qz[0][e]) + b * Xz;
+    }
 }
 
 template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY, bool NL, bool TS, bool TMA>
@@ -1096,12 +1177,17 @@ k_pressure(const __grid_constant__ PresArgs<R, SS, SP> A)
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L::o_bar);
     if (TMA) {
         if (tx == 0 && ty == 0) {
-            mbar_init(bars, 1);
-            mbar_init(bars + 1, 1);
+            for (int b = 0; b < (L::RINGS ? 6 : 2); ++b) mbar_init(bars + b, 1);
             mbar_fence_init();
         }
         __syncthreads();
     }
+    if constexpr (L::RINGS) {   // v rings of planes z0-1 .. z0+1 (later planes two ahead, in the loop)
+        if (tx == 0 && ty == 0 && z0 < z1)
+            for (int kk = z0 - 1; kk <= z0 + 1; ++kk) pres_issue_rings<R, SS, SP, NM, BX, BY>(A, smem, kk, xb, yb);
+    }
+    // phase parity of the ring barrier of plane kk (first used by plane z0 - 1)
+    auto ring_parity = [&](int kk) { return (unsigned)((kk - z0 + 1) >> 2) & 1u; };
     bool timed_out = false;
     if (z0 < z1) pres_issue<R, SS, SP, DIM, NM, BX, BY, NL, TS, TMA>(A, smem, z0, x0, y, yb, row, hd);
     cp_commit();
@@ -1128,7 +1214,10 @@ k_pressure(const __grid_constant__ PresArgs<R, SS, SP> A)
         unsigned char *st = smem + buf * L::stage;
         const R(*svx)[SWX] = reinterpret_cast<const R(*)[SWX]>(smem + L::o_svx + buf * L::svx_stride);
         const R(*svy)[TW] = reinterpret_cast<const R(*)[TW]>(smem + L::o_svy + buf * L::svy_stride);
-        __syncthreads();
+        __syncthreads();                           // iteration k-1 is done with stage/tiles (k+1)&1
+        if constexpr (L::RINGS) {                  // ring slot of plane k-2 is free: plane k+2 into it
+            if (tx == 0 && ty == 0 && k + 2 <= z1) pres_issue_rings<R, SS, SP, NM, BX, BY>(A, smem, k + 2, xb, yb);
+        }
         if (k + 1 < z1) pres_issue<R, SS, SP, DIM, NM, BX, BY, NL, TS, TMA>(A, smem, k + 1, x0, y, yb, row, hd);
         cp_commit();
         const bool pml_z = G.wabs > 0 && (k < G.wabs || k >= G.nz - G.wabs);
@@ -1138,13 +1227,19 @@ k_pressure(const __grid_constant__ PresArgs<R, SS, SP> A)
         // bounded wait for the TMA copies of plane k (see the velocity sweep);
         // with TMA staging each thread has waited itself: no barrier needed
         if (TMA && !timed_out && !mbar_wait_bounded(bars + buf, (unsigned)((k - z0) >> 1) & 1u)) timed_out = true;
+        if constexpr (L::RINGS) {                  // v rings of planes k-1, k (earlier waits) and k+1
+            for (int kk = k == z0 ? z0 - 1 : k + 1; kk <= k + 1 && !timed_out; ++kk)
+                if (!mbar_wait_bounded(bars + 2 + (kk & 3), ring_parity(kk))) timed_out = true;
+        }
         if (!TMA) __syncthreads();
         Sm<SS>::ld(reinterpret_cast<const SS *>(st + L::o_qn) + e0, qz[7]);
         if (hd) {
             R qd[3][4];
             R pv[4], kd[4], bd[4], ps[NM][4];
             Sm<SS>::ld(reinterpret_cast<const SS *>(st + L::o_kd) + e0, kd);
-            if (TS) {
+            if constexpr (L::RINGS) {
+                pres_divergence_ts_rings<R, SS, SP, NM, BX, BY>(A, st, smem, qz, kd, k, x0, e0, qd);
+            } else if (TS) {
                 pres_divergence_ts<R, SS, SP, DIM, NM, BX, BY>(A, st, &svx[0][0], &svy[0][0], qz, kd, k, x0, y, e0, qd);
             } else {
             {
@@ -1268,6 +1363,8 @@ k_pressure(const __grid_constant__ PresArgs<R, SS, SP> A)
     if (TMA && timed_out) {
         atomicExch(&A.mon->timeout, 1);
         for (int k = max(z0, z1 - 2); k < z1; ++k) mbar_wait_bounded(bars + (k & 1), (unsigned)((k - z0) >> 1) & 1u);
+        if constexpr (L::RINGS)
+            for (int kk = max(z0 - 1, z1 - 3); kk <= z1; ++kk) mbar_wait_bounded(bars + 2 + (kk & 3), ring_parity(kk));
     }
     // ---- stability monitor: one atomic per warp ----
     float m = bad ? 0.0f : (float)fmin(pmax, R(3.0e38));

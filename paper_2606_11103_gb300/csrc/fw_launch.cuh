@@ -104,6 +104,10 @@ bool build_vel_maps_t(EncodeTiledFn encode, fw_medium *m)
              encode_map<SS>(encode, &q.rho_own, m, m->rho, TW, BP) &&
              (!m->nonlinear || encode_map<SS>(encode, &q.b2dt, m, m->b2dt, TW, BP));
         for (int n = 0; n < m->nmech && ok; ++n) ok = encode_map<SP>(encode, &q.psi[n], m, m->psi2[n], TW, BP);
+        if (m->time_order == 4)       // the time-space stencil's rings of v planes
+            ok = ok && encode_map<SS>(encode, &q.vx_ring, m, m->v[0], TW + 8, BP + 2) &&
+                 encode_map<SS>(encode, &q.vy_ring, m, m->v[1], TW + 8, BP + 7) &&
+                 encode_map<SS>(encode, &q.vz_ring, m, m->v[2], TW + 8, BP + 2);
         return ok;
     }
 }
