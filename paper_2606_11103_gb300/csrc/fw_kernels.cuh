@@ -11,8 +11,11 @@
 // Every field is read once and written once per sweep from HBM: each thread
 // owns 4 consecutive x points of one (x, y) column and walks the depth axis;
 // the depth-direction taps come from a register queue of 8 planes, the x and
-// y taps from a double-buffered shared-memory plane tile with halos, and all
-// global traffic is 128-bit (FP32) and coalesced.
+// y taps from a double-buffered shared-memory plane tile with halos.  The
+// next plane of every stream is staged in shared memory while the current
+// one is computed: by TMA tile copies completed on an mbarrier in the 3D
+// FP32-state instances (one thread issues one box per stream), by per-thread
+// cp.async copies otherwise.  Stores are 128-bit (FP32) and coalesced.
 //
 // Memory-variable update (Eq. relaxation_psi, midpoint time index): with the
 // derivative g of the current half step, psi_new = b psi_old + a g, and the
