@@ -584,7 +584,12 @@ __device__ __forceinline__ void vel_gradient_ts(const VelArgs<R, SS, SP> &A, con
     {
         const R *s = sp0 + (RO + ty) * SW + 4 * tx;
 #pragma unroll
-        for (int i = 0; i < 12; ++i) w[i] = s[i];
+        for (int q = 0; q < 3; ++q) {
+            R a4[4];
+            Sm<R>::ld(s + 4 * q, a4);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) w[4 * q + i] = a4[i];
+        }
     }
     const long long rowk = (long long)y * G.px;
     const bool okm = k >= 1, okp = k + 1 < G.nz;
@@ -605,11 +610,17 @@ __device__ __forceinline__ void vel_gradient_ts(const VelArgs<R, SS, SP> &A, con
         R um[5], up[6];                                   // rows y-1 (x0..x0+4), y+1 (x0-1..x0+4) of plane k
         {
             const R *s = sp0 + (RO + ty - 1) * SW + 4 + 4 * tx;
+            R a4[4];
+            Sm<R>::ld(s, a4);
 #pragma unroll
-            for (int i = 0; i < 5; ++i) um[i] = s[i];
-            const R *t = sp0 + (RO + ty + 1) * SW + 3 + 4 * tx;
+            for (int i = 0; i < 4; ++i) um[i] = a4[i];
+            um[4] = s[4];
+            const R *t = sp0 + (RO + ty + 1) * SW + 4 + 4 * tx;
+            Sm<R>::ld(t, a4);
 #pragma unroll
-            for (int i = 0; i < 6; ++i) up[i] = t[i];
+            for (int i = 0; i < 4; ++i) up[i + 1] = a4[i];
+            up[0] = t[-1];
+            up[5] = t[4];
         }
         R a1m[4], a1p[4], am1p[4];                        // rows y+1 of planes k-1, k+1; row y-1 of plane k+1
         const bool oy1 = y + 1 < G.ny, oym = y >= 1;
@@ -623,6 +634,11 @@ __device__ __forceinline__ void vel_gradient_ts(const VelArgs<R, SS, SP> &A, con
             X[2][e] += (am1p[e] - um[e]) + (a1p[e] - up[e + 1]);
         }
     }
+    // y taps: rows y-3 .. y+4 of plane k, this thread's four columns
+    R cy[8][4];
+    if (DIM == 3)
+#pragma unroll
+        for (int r = 0; r < 8; ++r) Sm<R>::ld(sp0 + (RO + ty - 3 + r) * SW + 4 + 4 * tx, cy[r]);
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
         const bool live = x0 + e < G.nx;
@@ -631,13 +647,9 @@ __device__ __forceinline__ void vel_gradient_ts(const VelArgs<R, SS, SP> &A, con
         ts_weights(G, r2, a, b);
         g[0][e] = a[0] * (w[e + 5] - w[e + 4]) + a[1] * (w[e + 6] - w[e + 3]) + a[2] * (w[e + 7] - w[e + 2]) +
                   a[3] * (w[e + 8] - w[e + 1]) + b * X[0][e];
-        if (DIM == 3) {
-            const R *c = sp0 + 4 + 4 * tx + e;
-            g[1][e] = a[0] * (c[(RO + ty + 1) * SW] - c[(RO + ty) * SW]) +
-                      a[1] * (c[(RO + ty + 2) * SW] - c[(RO + ty - 1) * SW]) +
-                      a[2] * (c[(RO + ty + 3) * SW] - c[(RO + ty - 2) * SW]) +
-                      a[3] * (c[(RO + ty + 4) * SW] - c[(RO + ty - 3) * SW]) + b * X[1][e];
-        }
+        if (DIM == 3)
+            g[1][e] = a[0] * (cy[4][e] - cy[3][e]) + a[1] * (cy[5][e] - cy[2][e]) + a[2] * (cy[6][e] - cy[1][e]) +
+                      a[3] * (cy[7][e] - cy[0][e]) + b * X[1][e];
         g[2][e] = a[0] * (q[4][e] - q[3][e]) + a[1] * (q[5][e] - q[2][e]) + a[2] * (q[6][e] - q[1][e]) +
                   a[3] * (q[7][e] - q[0][e]) + b * X[2][e];
     }
@@ -938,38 +950,110 @@ __device__ __forceinline__ void pres_divergence_ts_rings(const PresArgs<R, SS, S
     auto rx = [&](int kk) { return reinterpret_cast<const R *>(sm + L::o_rx + (kk & 3) * L::rx_stride); };
     auto ry = [&](int kk) { return reinterpret_cast<const R *>(sm + L::o_ry + (kk & 3) * L::ry_stride); };
     auto rz = [&](int kk) { return reinterpret_cast<const R *>(sm + L::o_rz + (kk & 3) * L::rx_stride); };
-    const R *xk = rx(k), *xm = rx(k - 1), *xp = rx(k + 1);
-    const R *yk = ry(k), *ym = ry(k - 1), *yp = ry(k + 1);
-    const R *zk = rz(k), *zm = rz(k - 1);
+    const int c0 = 4 + 4 * tx;                     // column of x0 in the ring tiles (a multiple of 4)
+    const int rX = ty + 1, rY = ty + 4;            // row of y in the v_x / v_z and in the v_y tiles
+    // eight values at columns c0-4 .. c0+3 of row r of tile t (two 16-byte loads)
+    auto row8 = [&](const R *t, int r, R (&o)[8]) {
+        R a4[4], b4[4];
+        Sm<R>::ld(t + r * SW + c0 - 4, a4);
+        Sm<R>::ld(t + r * SW + c0, b4);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) { o[i] = a4[i]; o[i + 4] = b4[i]; }
+    };
+    R X[3][4], t8[8];
+    // v_x: two-point x differences at x (v(x) - v(x-1)) of rows y -+ 1 (plane k) and of planes k -+ 1 (row y)
+    {
+        const R *xs[4] = {rx(k), rx(k), rx(k - 1), rx(k + 1)};
+        const int rs[4] = {rX - 1, rX + 1, rX, rX};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) X[0][e] = R(0);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            row8(xs[j], rs[j], t8);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) X[0][e] += t8[e + 4] - t8[e + 3];
+        }
+    }
+    // v_y: two-point y differences at y (v(y) - v(y-1)) at columns x -+ 1 (plane k) and of planes k -+ 1
+    {
+        const R *yk = ry(k);
+        R u0[4], u1[4];
+        Sm<R>::ld(yk + rY * SW + c0, u0);
+        Sm<R>::ld(yk + (rY - 1) * SW + c0, u1);
+        const R l0 = yk[rY * SW + c0 - 1], l1 = yk[(rY - 1) * SW + c0 - 1];
+        const R g0 = yk[rY * SW + c0 + 4], g1 = yk[(rY - 1) * SW + c0 + 4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const R am = e > 0 ? u0[e - 1] - u1[e - 1] : l0 - l1;
+            const R ap = e < 3 ? u0[e + 1] - u1[e + 1] : g0 - g1;
+            X[1][e] = am + ap;
+        }
+#pragma unroll
+        for (int s = -1; s <= 1; s += 2) {
+            const R *yp = ry(k + s);
+            Sm<R>::ld(yp + rY * SW + c0, u0);
+            Sm<R>::ld(yp + (rY - 1) * SW + c0, u1);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) X[1][e] += u0[e] - u1[e];
+        }
+    }
+    // v_z: two-point depth differences (plane k minus k-1) at x -+ 1 (row y) and at y -+ 1
+    {
+        const R *zk = rz(k), *zm = rz(k - 1);
+        R d[6];                                    // columns c0-1 .. c0+4 of row y, plane k minus plane k-1
+        {
+            R a4[4], b4[4];
+            Sm<R>::ld(zk + rX * SW + c0, a4);
+            Sm<R>::ld(zm + rX * SW + c0, b4);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) d[e + 1] = a4[e] - b4[e];
+            d[0] = zk[rX * SW + c0 - 1] - zm[rX * SW + c0 - 1];
+            d[5] = zk[rX * SW + c0 + 4] - zm[rX * SW + c0 + 4];
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) X[2][e] = d[e] + d[e + 2];
+#pragma unroll
+        for (int s = -1; s <= 1; s += 2) {
+            R a4[4], b4[4];
+            Sm<R>::ld(zk + (rX + s) * SW + c0, a4);
+            Sm<R>::ld(zm + (rX + s) * SW + c0, b4);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) X[2][e] += a4[e] - b4[e];
+        }
+    }
+    // on-axis x: columns c0-4 .. c0+7 of row y, plane k
+    R w[12];
+    {
+        const R *xk = rx(k);
+        R a4[4];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            Sm<R>::ld(xk + rX * SW + c0 - 4 + 4 * q, a4);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) w[4 * q + i] = a4[i];
+        }
+    }
+    // on-axis y: rows y-4 .. y+3 of plane k, this thread's four columns
+    R cy[8][4];
+    {
+        const R *yk = ry(k);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) Sm<R>::ld(yk + (rY - 4 + r) * SW + c0, cy[r]);
+    }
     R rh[4];
     Sm<SS>::ld(reinterpret_cast<const SS *>(st + L::o_rh) + e0, rh);
-    const int c0 = 4 + 4 * tx;                     // column of x0 in the ring tiles
-    const int rX = ty + 1, rY = ty + 4;            // row of y in the v_x / v_z and in the v_y tiles
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-        const int c = c0 + e;
         const bool live = x0 + e < G.nx;
         const R r2 = live ? kd[e] * G.r2s * fw_rcp(rh[e]) : R(0);
         R a[4], b;
         ts_weights(G, r2, a, b);
-        // v_x: x-derivative at x (v_x(i) - v_x(i-1) pairs), cross terms at y -+ 1 and planes k -+ 1
-        const R *w = xk + rX * SW;
-        const R Xx = (xk[(rX - 1) * SW + c] - xk[(rX - 1) * SW + c - 1]) + (xk[(rX + 1) * SW + c] - xk[(rX + 1) * SW + c - 1]) +
-                     (xm[rX * SW + c] - xm[rX * SW + c - 1]) + (xp[rX * SW + c] - xp[rX * SW + c - 1]);
-        qd[0][e] = a[0] * (w[c] - w[c - 1]) + a[1] * (w[c + 1] - w[c - 2]) + a[2] * (w[c + 2] - w[c - 3]) +
-                   a[3] * (w[c + 3] - w[c - 4]) + b * Xx;
-        // v_y: y-derivative at y (v_y(j) - v_y(j-1)), cross terms at x -+ 1 and planes k -+ 1
-        const R *v = yk + c;
-        const R Xy = (yk[rY * SW + c - 1] - yk[(rY - 1) * SW + c - 1]) + (yk[rY * SW + c + 1] - yk[(rY - 1) * SW + c + 1]) +
-                     (ym[rY * SW + c] - ym[(rY - 1) * SW + c]) + (yp[rY * SW + c] - yp[(rY - 1) * SW + c]);
-        qd[1][e] = a[0] * (v[rY * SW] - v[(rY - 1) * SW]) + a[1] * (v[(rY + 1) * SW] - v[(rY - 2) * SW]) +
-                   a[2] * (v[(rY + 2) * SW] - v[(rY - 3) * SW]) + a[3] * (v[(rY + 3) * SW] - v[(rY - 4) * SW]) +
-                   b * Xy;
-        // v_z: depth derivative from the queue, cross terms at x -+ 1 and y -+ 1 (planes k, k-1)
-        const R Xz = (zk[rX * SW + c - 1] - zm[rX * SW + c - 1]) + (zk[rX * SW + c + 1] - zm[rX * SW + c + 1]) +
-                     (zk[(rX - 1) * SW + c] - zm[(rX - 1) * SW + c]) + (zk[(rX + 1) * SW + c] - zm[(rX + 1) * SW + c]);
+        qd[0][e] = a[0] * (w[e + 4] - w[e + 3]) + a[1] * (w[e + 5] - w[e + 2]) + a[2] * (w[e + 6] - w[e + 1]) +
+                   a[3] * (w[e + 7] - w[e + 0]) + b * X[0][e];
+        qd[1][e] = a[0] * (cy[4][e] - cy[3][e]) + a[1] * (cy[5][e] - cy[2][e]) + a[2] * (cy[6][e] - cy[1][e]) +
+                   a[3] * (cy[7][e] - cy[0][e]) + b * X[1][e];
         qd[2][e] = a[0] * (qz[4][e] - qz[3][e]) + a[1] * (qz[5][e] - qz[2][e]) + a[2] * (qz[6][e] - qz[1][e]) +
-                   a[3] * (qz[7][e] - qz[0][e]) + b * Xz;
+                   a[3] * (qz[7][e] - qz[0][e]) + b * X[2][e];
     }
 }
 
