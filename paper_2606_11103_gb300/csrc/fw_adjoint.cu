@@ -23,16 +23,18 @@
 // (in the absorbing layer a -> r a and ceff -> 1/kappa + r (ceff - 1/kappa),
 // r the tissue ramp of the cell);
 // with (D+)^T = -D- and (D-)^T = -D+ for zero values beyond the grid.
-// One reverse step is five launches: receiver injection, source-gain
-// gradient, pressure adjoint (pointwise, writes the adjoint of q_d), velocity
-// adjoint (stencil of that, pointwise, writes the adjoint of g_d), and the
-// stencil update of the pressure adjoint.  Gradients accumulate in FP64.
+// A reverse step is receiver injection and the source-gain gradient, then the
+// pressure adjoint (pointwise; gives the adjoint of q_d), the velocity adjoint
+// (a stencil of that, pointwise; gives the adjoint of g_d) and the stencil
+// update of the pressure adjoint: one tiled kernel in 2D, three kernels in 3D.
+// Gradients accumulate in FP64.
 // The linear system only (no nonlinear factor); FP32 and FP64 media.
 #include "fw_internal.h"
 #include "fw_kernels.cuh"
 
 #include <algorithm>
 #include <cmath>
+#include <utility>
 #include <vector>
 
 namespace fwgb {
@@ -47,6 +49,11 @@ namespace {
 
 constexpr int kDStride = 16;   // derivative table per class: dA1[4], dB1[4], dA2[4], dB2[4]
 
+// adjoint state: p, v_d, the memory variables of both sides and of the absorbing layer
+template <typename R> struct AdjState {
+    R *lp, *lv[3], *lpsi1[kMaxMech][3], *lpsi2[kMaxMech], *lpsi1p[3], *lpsi2p[3];
+};
+
 template <typename R> struct AdjArgs {
     int nx, ny, nz, px, nmech;
     long long plane, vol;
@@ -54,8 +61,9 @@ template <typename R> struct AdjArgs {
     R c1, c2, c3, c4, dt;
     int wabs;          // absorbing width (0: none) and 1 / length of the tissue ramp
     R inv_lr;
-    // adjoint state
-    R *lp, *lv[3], *lpsi1[kMaxMech][3], *lpsi2[kMaxMech], *lpsi1p[3], *lpsi2p[3];
+    // adjoint state after the step (read) and before it (written; the same buffer
+    // for the three-kernel form, the other buffer of a pair for the one-kernel form)
+    AdjState<R> in, out;
     // forward state before the step (f) and velocity after it (fv1)
     const R *fp, *fpsi1[kMaxMech][3], *fpsi2[kMaxMech], *fpsi2p[3];
     const R *fv1[3];
@@ -64,7 +72,7 @@ template <typename R> struct AdjArgs {
     const uint16_t *cls;
     const R *lut, *dlut;
     const R *pdh[3], *pah[3], *pdi[3], *pai[3];   // absorbing profile at half / integer points
-    // scratch: adjoints of q_d and of g_d
+    // scratch of the three-kernel form: adjoints of q_d and of g_d
     R *Q[3], *Gd[3];
     double *gk, *gs;
 };
@@ -75,6 +83,16 @@ template <typename R> struct Pt {
     long long st[3];   // strides
 };
 
+template <typename R>
+__device__ __forceinline__ Pt<R> make_pt(const AdjArgs<R> &A, int x, int y, int z)
+{
+    Pt<R> p;
+    p.c[0] = x; p.c[1] = y; p.c[2] = z;
+    p.n[0] = A.nx; p.n[1] = A.ny; p.n[2] = A.nz;
+    p.st[0] = 1; p.st[1] = A.px; p.st[2] = A.plane;
+    return p;
+}
+
 // One thread per point: x from the block's x range and thread, the other two
 // kernel axes from the grid's y and z (no division of a flat index).
 template <typename R>
@@ -82,11 +100,7 @@ __device__ __forceinline__ bool point(const AdjArgs<R> &A, Pt<R> &p, long long &
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= A.nx) return false;
-    p.c[0] = x;
-    p.c[1] = blockIdx.y;
-    p.c[2] = blockIdx.z;
-    p.n[0] = A.nx; p.n[1] = A.ny; p.n[2] = A.nz;
-    p.st[0] = 1; p.st[1] = A.px; p.st[2] = A.plane;
+    p = make_pt(A, x, (int)blockIdx.y, (int)blockIdx.z);
     i = (long long)blockIdx.z * A.plane + (long long)blockIdx.y * A.px + x;
     return true;
 }
@@ -95,7 +109,7 @@ __device__ __forceinline__ bool point(const AdjArgs<R> &A, Pt<R> &p, long long &
 template <typename R>
 __device__ __forceinline__ R dplus(const AdjArgs<R> &A, const R *f, long long i, int c, int n, long long st)
 {
-    auto at = [&](int cc) -> R { return (cc >= 0 && cc < n) ? f[i + (long long)(cc - c) * st] : R(0); };
+    auto at = [&](int cc) -> R { return (cc >= 0 && cc < n) ? __ldg(f + i + (long long)(cc - c) * st) : R(0); };
     return A.c1 * (at(c + 1) - at(c)) + A.c2 * (at(c + 2) - at(c - 1)) + A.c3 * (at(c + 3) - at(c - 2)) +
            A.c4 * (at(c + 4) - at(c - 3));
 }
@@ -104,9 +118,25 @@ __device__ __forceinline__ R dplus(const AdjArgs<R> &A, const R *f, long long i,
 template <typename R>
 __device__ __forceinline__ R dminus(const AdjArgs<R> &A, const R *f, long long i, int c, int n, long long st)
 {
-    auto at = [&](int cc) -> R { return (cc >= 0 && cc < n) ? f[i + (long long)(cc - c) * st] : R(0); };
+    auto at = [&](int cc) -> R { return (cc >= 0 && cc < n) ? __ldg(f + i + (long long)(cc - c) * st) : R(0); };
     return A.c1 * (at(c) - at(c - 1)) + A.c2 * (at(c + 1) - at(c - 2)) + A.c3 * (at(c + 2) - at(c - 3)) +
            A.c4 * (at(c + 3) - at(c - 4));
+}
+
+// the same two differences of a run of values in shared memory (f[k] at the point + k,
+// zero beyond the grid already stored)
+template <typename R>
+__device__ __forceinline__ R dplus_s(const AdjArgs<R> &A, const R *f, int st)
+{
+    return A.c1 * (f[st] - f[0]) + A.c2 * (f[2 * st] - f[-st]) + A.c3 * (f[3 * st] - f[-2 * st]) +
+           A.c4 * (f[4 * st] - f[-3 * st]);
+}
+
+template <typename R>
+__device__ __forceinline__ R dminus_s(const AdjArgs<R> &A, const R *f, int st)
+{
+    return A.c1 * (f[0] - f[-st]) + A.c2 * (f[st] - f[-2 * st]) + A.c3 * (f[2 * st] - f[-3 * st]) +
+           A.c4 * (f[3 * st] - f[-4 * st]);
 }
 
 // tissue-mechanism strength of the cell (the forward sweeps' ramp, same arithmetic)
@@ -119,62 +149,131 @@ __device__ __forceinline__ R cell_ramp(const AdjArgs<R> &A, const Pt<R> &P)
     return ramp_of(s, A.inv_lr);
 }
 
-template <typename R, int DIM, int NM>
-__global__ void k_adj_pres(const AdjArgs<R> A)
+// Pressure adjoint at an in-grid point i: the adjoints of q_d (Qv).  FULL also
+// takes the gradient terms of the step (gs, gk) and writes the memory
+// variables before the step; without FULL only the adjoint state is read
+// (the halo of the one-kernel form).
+template <typename R, int DIM, int NM, bool FULL>
+__device__ __forceinline__ void pres_point(const AdjArgs<R> &A, const Pt<R> &P, long long i, R (&Qv)[3], R &gs,
+                                           double &gk)
 {
-    Pt<R> P;
-    long long i;
-    if (!point(A, P, i)) return;
-    {
-        const R *t = A.lut + (size_t)A.cls[i] * kLutStride;
-        const R *dtb = A.dlut + (size_t)A.cls[i] * kDStride;
-        R q[3] = {0, 0, 0}, div = 0;
+    const int cl = __ldg(A.cls + i);
+    const R *t = A.lut + (size_t)cl * kLutStride;
+    const R *dtb = A.dlut + (size_t)cl * kDStride;
+    R q[3] = {0, 0, 0}, div = 0;
+    if (FULL) {
 #pragma unroll
         for (int ax = 0; ax < 3; ++ax)
             if (DIM == 3 || ax != 1) {
                 q[ax] = dminus(A, A.fv1[ax], i, P.c[ax], P.n[ax], P.st[ax]);
                 div += q[ax];
             }
-        const R lp = A.lp[i];
-        const R lst = -A.kdt[i] * lp;
-        // tissue ramp of the absorbing layer: a -> r a (the forward sweep's ce, r div)
-        const R r = cell_ramp(A, P);
-        const R ce = t[3] + (r - R(1)) * t[kLutDk + 1];   // the forward sweep's ceff
-        R stp = div * ce;
-        R ldiv = ce * lst;
-        // this step's terms in the working precision; the sum over steps in FP64
-        // (FP64 arithmetic is slow on this GPU: one addition per point and step)
-        R gs = 0;
+    }
+    const R lp = __ldg(A.in.lp + i);
+    const R lst = -__ldg(A.kdt + i) * lp;
+    // tissue ramp of the absorbing layer: a -> r a (the forward sweep's ce, r div)
+    const R r = cell_ramp(A, P);
+    const R ce = __ldg(t + 3) + (r - R(1)) * __ldg(t + kLutDk + 1);   // the forward sweep's ceff
+    R stp = div * ce;
+    R ldiv = ce * lst;
+    // this step's terms in the working precision; the sum over steps in FP64
+    // (FP64 arithmetic is slow on this GPU: one addition per point and step)
+    gs = 0;
 #pragma unroll
-        for (int m = 0; m < NM; ++m) {
-            const R old = A.fpsi2[m][i];
-            stp += t[kLutH2 + m] * old;
-            const R ln = A.lpsi2[m][i];
-            ldiv += r * t[kLutA2 + m] * ln;
-            gs += (dtb[12 + m] * old + r * dtb[8 + m] * div) * (ln + R(0.5) * lst);
-            A.lpsi2[m][i] = t[kLutB2 + m] * ln + t[kLutH2 + m] * lst;
+    for (int m = 0; m < NM; ++m) {
+        const R ln = __ldg(A.in.lpsi2[m] + i);
+        ldiv += r * __ldg(t + kLutA2 + m) * ln;
+        if (FULL) {
+            const R old = __ldg(A.fpsi2[m] + i);
+            stp += __ldg(t + kLutH2 + m) * old;
+            gs += (__ldg(dtb + 12 + m) * old + r * __ldg(dtb + 8 + m) * div) * (ln + R(0.5) * lst);
+            A.out.lpsi2[m][i] = __ldg(t + kLutB2 + m) * ln + __ldg(t + kLutH2 + m) * lst;
         }
+    }
 #pragma unroll
-        for (int ax = 0; ax < 3; ++ax) {
-            if (DIM == 2 && ax == 1) continue;
-            R qv = ldiv;
-            if (A.pdi[ax]) {
-                const R d = A.pdi[ax][P.c[ax]];
-                if (d > R(0)) {
-                    R a, b;
-                    pml_ab(d, A.pai[ax][P.c[ax]], t[1], A.dt, a, b);
-                    const R old = A.fpsi2p[ax][i];
+    for (int ax = 0; ax < 3; ++ax) {
+        if (DIM == 2 && ax == 1) continue;
+        R qv = ldiv;
+        if (A.pdi[ax]) {
+            const R d = __ldg(A.pdi[ax] + P.c[ax]);
+            if (d > R(0)) {
+                R a, b;
+                pml_ab(d, __ldg(A.pai[ax] + P.c[ax]), __ldg(t + 1), A.dt, a, b);
+                const R ln = __ldg(A.in.lpsi2p[ax] + i);
+                qv += a * (ln + R(0.5) * lst);
+                if (FULL) {
+                    const R old = __ldg(A.fpsi2p[ax] + i);
                     stp += R(0.5) * (R(1) + b) * old + R(0.5) * a * q[ax];
-                    const R ln = A.lpsi2p[ax][i];
-                    qv += a * (ln + R(0.5) * lst);
-                    A.lpsi2p[ax][i] = b * ln + R(0.5) * (R(1) + b) * lst;
+                    A.out.lpsi2p[ax][i] = b * ln + R(0.5) * (R(1) + b) * lst;
                 }
             }
-            A.Q[ax][i] = qv;
         }
-        A.gk[i] += double(-stp * lp);
-        A.gs[i] += double(gs);
+        Qv[ax] = qv;
     }
+    gk = FULL ? double(-stp * lp) : 0.0;
+}
+
+// Velocity adjoint along axis ax at an in-grid point i, given dq = D+ of the
+// adjoint of q_ax there: returns the adjoint of g_ax.  FULL also adds the
+// gradient terms to gs and writes v_ax and the memory variables before the
+// step.
+template <typename R, int NM, bool FULL, int ax>
+__device__ __forceinline__ R vel_point(const AdjArgs<R> &A, const Pt<R> &P, long long i, R dq, R &gs)
+{
+    const int cl = __ldg(A.cls + i);
+    const R *t = A.lut + (size_t)cl * kLutStride;
+    const R *dtb = A.dlut + (size_t)cl * kDStride;
+    const R own = __ldg(A.rho + i);
+    const R r = cell_ramp(A, P);
+    const R ce = __ldg(t + 2) + (r - R(1)) * __ldg(t + kLutDk);
+    const int c = P.c[ax], n = P.n[ax];
+    const long long st = P.st[ax];
+    const R lv = __ldg(A.in.lv[ax] + i) - dq;
+    const R nxt = (c + 1 < n) ? __ldg(A.rho + i + st) : own;
+    const R dtr = R(2) * A.dt * fw_rcp(own + nxt);
+    const R lst = -dtr * lv;
+    const R g = FULL ? dplus(A, A.fp, i, c, n, st) : R(0);
+    R lg = ce * lst;
+#pragma unroll
+    for (int m = 0; m < NM; ++m) {
+        const R ln = __ldg(A.in.lpsi1[m][ax] + i);
+        lg += r * __ldg(t + kLutA1 + m) * ln;
+        if (FULL) {
+            const R old = __ldg(A.fpsi1[m][ax] + i);
+            gs += (__ldg(dtb + 4 + m) * old + r * __ldg(dtb + m) * g) * (ln + R(0.5) * lst);
+            A.out.lpsi1[m][ax][i] = __ldg(t + kLutB1 + m) * ln + __ldg(t + kLutH1 + m) * lst;
+        }
+    }
+    if (A.pdh[ax]) {
+        const R d = __ldg(A.pdh[ax] + c);
+        if (d > R(0)) {
+            R a, b;
+            pml_ab(d, __ldg(A.pah[ax] + c), __ldg(t), A.dt, a, b);
+            const R ln = __ldg(A.in.lpsi1p[ax] + i);
+            lg += a * (ln + R(0.5) * lst);
+            if (FULL) A.out.lpsi1p[ax][i] = b * ln + R(0.5) * (R(1) + b) * lst;
+        }
+    }
+    if (FULL) A.out.lv[ax][i] = lv;
+    return lg;
+}
+
+// ---- three-kernel form (3D): adjoints of q_d and g_d through global scratch ----
+
+template <typename R, int DIM, int NM>
+__global__ void k_adj_pres(const AdjArgs<R> A)
+{
+    Pt<R> P;
+    long long i;
+    if (!point(A, P, i)) return;
+    R Qv[3], gs;
+    double gk;
+    pres_point<R, DIM, NM, true>(A, P, i, Qv, gs, gk);
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax)
+        if (DIM == 3 || ax != 1) A.Q[ax][i] = Qv[ax];
+    A.gk[i] += gk;
+    A.gs[i] += double(gs);
 }
 
 template <typename R, int DIM, int NM>
@@ -183,47 +282,16 @@ __global__ void k_adj_vel(const AdjArgs<R> A)
     Pt<R> P;
     long long i;
     if (!point(A, P, i)) return;
-    {
-        const R *t = A.lut + (size_t)A.cls[i] * kLutStride;
-        const R *dtb = A.dlut + (size_t)A.cls[i] * kDStride;
-        const R own = A.rho[i];
-        const R r = cell_ramp(A, P);
-        const R ce = t[2] + (r - R(1)) * t[kLutDk];
-        R gs = 0;   // this step's terms; the sum over steps in FP64
+    R gs = 0;   // this step's terms; the sum over steps in FP64
 #pragma unroll
-        for (int ax = 0; ax < 3; ++ax) {
-            if (DIM == 2 && ax == 1) continue;
-            const int c = P.c[ax], n = P.n[ax];
-            const long long st = P.st[ax];
-            const R lv = A.lv[ax][i] - dplus(A, A.Q[ax], i, c, n, st);
-            const R nxt = (c + 1 < n) ? A.rho[i + st] : own;
-            const R dtr = R(2) * A.dt * fw_rcp(own + nxt);
-            const R lst = -dtr * lv;
-            const R g = dplus(A, A.fp, i, c, n, st);
-            R lg = ce * lst;
-#pragma unroll
-            for (int m = 0; m < NM; ++m) {
-                const R old = A.fpsi1[m][ax][i];
-                const R ln = A.lpsi1[m][ax][i];
-                lg += r * t[kLutA1 + m] * ln;
-                gs += (dtb[4 + m] * old + r * dtb[m] * g) * (ln + R(0.5) * lst);
-                A.lpsi1[m][ax][i] = t[kLutB1 + m] * ln + t[kLutH1 + m] * lst;
-            }
-            if (A.pdh[ax]) {
-                const R d = A.pdh[ax][c];
-                if (d > R(0)) {
-                    R a, b;
-                    pml_ab(d, A.pah[ax][c], t[0], A.dt, a, b);
-                    const R ln = A.lpsi1p[ax][i];
-                    lg += a * (ln + R(0.5) * lst);
-                    A.lpsi1p[ax][i] = b * ln + R(0.5) * (R(1) + b) * lst;
-                }
-            }
-            A.Gd[ax][i] = lg;
-            A.lv[ax][i] = lv;
-        }
-        A.gs[i] += double(gs);
+    for (int ax = 0; ax < 3; ++ax) {
+        if (DIM == 2 && ax == 1) continue;
+        const R dq = dplus(A, A.Q[ax], i, P.c[ax], P.n[ax], P.st[ax]);
+        A.Gd[ax][i] = ax == 0   ? vel_point<R, NM, true, 0>(A, P, i, dq, gs)
+                      : ax == 1 ? vel_point<R, NM, true, 1>(A, P, i, dq, gs)
+                                : vel_point<R, NM, true, 2>(A, P, i, dq, gs);
     }
+    A.gs[i] += double(gs);
 }
 
 template <typename R, int DIM, int NM>
@@ -232,13 +300,11 @@ __global__ void k_adj_p(const AdjArgs<R> A)
     Pt<R> P;
     long long i;
     if (!point(A, P, i)) return;
-    {
-        R s = 0;
+    R s = 0;
 #pragma unroll
-        for (int ax = 0; ax < 3; ++ax)
-            if (DIM == 3 || ax != 1) s += dminus(A, A.Gd[ax], i, P.c[ax], P.n[ax], P.st[ax]);
-        A.lp[i] -= s;
-    }
+    for (int ax = 0; ax < 3; ++ax)
+        if (DIM == 3 || ax != 1) s += dminus(A, A.Gd[ax], i, P.c[ax], P.n[ax], P.st[ax]);
+    A.out.lp[i] = A.in.lp[i] - s;
 }
 
 template <typename R>
@@ -300,33 +366,258 @@ __global__ void k_grad_out(const double *uc, const double *us, const float *a0f,
     }
 }
 
-// the three adjoint kernels of one reverse step, instantiated per dimension
-// and number of mechanisms (their loops unroll)
-template <typename R, int DIM, int NM>
-void launch_reverse_dn(const AdjArgs<R> &A, dim3 grid, cudaStream_t s)
+// ---- one-kernel form (2D): the whole reverse step per tile ----
+//
+// A CTA owns a TX x TZ tile of the (x, z) grid.  The adjoints of q_d and g_d
+// stay in shared memory over the tile and the halo their two stencils need
+// along their own axis: g_d on 4 points before and 3 after the tile (the
+// backward difference of the last update), q_d on 7 before and 7 after (the
+// forward difference that gives g_d there).  Each CTA recomputes its halo from
+// the adjoint state after the step, which it reads from one buffer while it
+// writes the state before the step to the other (a neighbour still reads the
+// old values).
+// tuning overrides: FWGB_ADJ_TX / FWGB_ADJ_TZ (tile), FWGB_ADJ_THREADS
+#ifndef FWGB_ADJ_THREADS
+#define FWGB_ADJ_THREADS 256
+#endif
+#ifndef FWGB_ADJ_TX
+#define FWGB_ADJ_TX 32
+#endif
+#ifndef FWGB_ADJ_TZ
+#define FWGB_ADJ_TZ 32
+#endif
+constexpr int kAdjThreads = FWGB_ADJ_THREADS;
+
+template <int TX, int TZ> struct AdjTile {
+    static constexpr int QXW = TX + 14, QZH = TZ + 14;   // q_x rows, q_z columns
+    static constexpr int GXW = TX + 7, GZH = TZ + 7;     // g_x rows, g_z columns
+    static constexpr int n_qx = TZ * QXW, n_qz = QZH * TX, n_gx = TZ * GXW, n_gz = GZH * TX;
+    static constexpr int elems = n_qx + n_qz + n_gx + n_gz;
+    static constexpr int NI = TX * TZ / kAdjThreads;     // tile points per thread
+    static_assert(TX * TZ % kAdjThreads == 0, "tile points split evenly over the threads");
+};
+
+#ifndef FWGB_ADJ_PREFETCH
+#define FWGB_ADJ_PREFETCH 2   // 0: none, 1: both sides at the start, 2: velocity side after the tile's q_d
+#endif
+
+// Bulk prefetch into L2 of the elements [xa, xb) of row z of a field, clamped
+// to the row (rows are 128-byte aligned, so the 16-byte rounding stays inside).
+template <typename R, typename T>
+__device__ __forceinline__ void prefetch_row(const AdjArgs<R> &A, const T *f, int z, int xa, int xb)
 {
-    k_adj_pres<R, DIM, NM><<<grid, 256, 0, s>>>(A);
-    k_adj_vel<R, DIM, NM><<<grid, 256, 0, s>>>(A);
-    k_adj_p<R, DIM, NM><<<grid, 256, 0, s>>>(A);
+    xa = max(xa, 0);
+    xb = min(xb, A.px);
+    if (!f || z < 0 || z >= A.nz || xa >= xb) return;
+    const size_t b = __cvta_generic_to_global(f + (long long)z * A.plane + xa) & ~size_t(15);
+    const size_t e = (__cvta_generic_to_global(f + (long long)z * A.plane + xb) + 15) & ~size_t(15);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(b), "r"((unsigned)(e - b)) : "memory");
+}
+
+// The fields one side of the reverse step reads on a tile (side 0: pressure
+// adjoint, side 1: velocity adjoint), field f of that side: its pointer and
+// whether it is read on the q_d halo box (else on the tile with a 4-point
+// stencil halo).
+template <typename R, int NM>
+__device__ __forceinline__ int side_fields(int side) { return side == 0 ? 6 + 2 * NM : 5 + 4 * NM; }
+
+template <typename R, int NM>
+__device__ __forceinline__ void side_field(const AdjArgs<R> &A, int side, int f, const void *&p, int &es, bool &box)
+{
+    es = sizeof(R);
+    box = true;
+    if (side == 0) {
+        if (f == 0) p = A.in.lp;
+        else if (f == 1) p = A.kdt;
+        else if (f == 2) { p = A.cls; es = 2; }
+        else if (f < 3 + NM) p = A.in.lpsi2[f - 3];
+        else {
+            box = false;
+            f -= 3 + NM;
+            if (f == 0) p = A.fv1[0];
+            else if (f == 1) p = A.fv1[2];
+            else if (f == 2) { p = A.gk; es = 8; }
+            else p = A.fpsi2[f - 3];
+        }
+    } else {
+        if (f == 0) p = A.in.lv[0];
+        else if (f == 1) p = A.in.lv[2];
+        else if (f == 2) p = A.rho;
+        else if (f < 3 + NM) p = A.in.lpsi1[f - 3][0];
+        else if (f < 3 + 2 * NM) p = A.in.lpsi1[f - 3 - NM][2];
+        else {
+            box = false;
+            f -= 3 + 2 * NM;
+            if (f == 0) p = A.fp;
+            else if (f == 1) { p = A.gs; es = 8; }
+            else if (f < 2 + NM) p = A.fpsi1[f - 2][0];
+            else p = A.fpsi1[f - 2 - NM][2];
+        }
+    }
+}
+
+template <typename R, int NM, int TX, int TZ>
+__device__ __forceinline__ void prefetch_side(const AdjArgs<R> &A, int side, int x0, int z0)
+{
+    constexpr int ROWS = TZ + 14;
+    const int n = side_fields<R, NM>(side) * ROWS;
+    for (int j = threadIdx.x; j < n; j += kAdjThreads) {
+        const int f = j / ROWS, r = j % ROWS;
+        const void *p;
+        int es;
+        bool box;
+        side_field<R, NM>(A, side, f, p, es, box);
+        const int h = box ? 7 : 4;
+        if (r >= TZ + 2 * h) continue;
+        const int z = z0 - h + r, xa = x0 - h, xb = x0 + TX + h;
+        if (es == 2) prefetch_row(A, static_cast<const uint16_t *>(p), z, xa, xb);
+        else if (es == 4) prefetch_row(A, static_cast<const float *>(p), z, xa, xb);
+        else prefetch_row(A, static_cast<const double *>(p), z, xa, xb);
+    }
+}
+
+template <typename R, int NM, int TX, int TZ>
+__global__ void __launch_bounds__(kAdjThreads) k_adj_step2(const AdjArgs<R> A)
+{
+    using T = AdjTile<TX, TZ>;
+    extern __shared__ __align__(16) unsigned char adj_smem[];
+    R *sQx = reinterpret_cast<R *>(adj_smem);
+    R *sQz = sQx + T::n_qx;
+    R *sGx = sQz + T::n_qz;
+    R *sGz = sGx + T::n_gx;
+    const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ, tid = threadIdx.x;
+    auto inside = [&](int x, int z) { return x >= 0 && x < A.nx && z >= 0 && z < A.nz; };
+    auto at = [&](int x, int z) { return (long long)z * A.plane + x; };
+    R gsum[T::NI];
+    if (FWGB_ADJ_PREFETCH >= 1) prefetch_side<R, NM, TX, TZ>(A, 0, x0, z0);
+    if (FWGB_ADJ_PREFETCH == 1) prefetch_side<R, NM, TX, TZ>(A, 1, x0, z0);
+
+    // q_d: the tile (full pressure adjoint), then the wings
+#pragma unroll
+    for (int k = 0; k < T::NI; ++k) {
+        const int j = tid + k * kAdjThreads, lx = j % TX, lz = j / TX, x = x0 + lx, z = z0 + lz;
+        R Qv[3] = {0, 0, 0};
+        gsum[k] = 0;
+        if (inside(x, z)) {
+            double gk;
+            pres_point<R, 2, NM, true>(A, make_pt(A, x, 0, z), at(x, z), Qv, gsum[k], gk);
+            A.gk[at(x, z)] += gk;
+        }
+        sQx[lz * T::QXW + lx + 7] = Qv[0];
+        sQz[(lz + 7) * TX + lx] = Qv[2];
+    }
+    if (FWGB_ADJ_PREFETCH == 2) prefetch_side<R, NM, TX, TZ>(A, 1, x0, z0);
+    for (int j = tid; j < 14 * (TZ + TX); j += kAdjThreads) {
+        int lx, lz, ax;
+        if (j < 14 * TZ) {   // q_x: 7 points either side of each tile row
+            const int w = j % 14;
+            lz = j / 14;
+            lx = w < 7 ? w - 7 : TX + w - 7;
+            ax = 0;
+        } else {             // q_z: 7 rows above and below the tile
+            const int jj = j - 14 * TZ, w = jj / TX;
+            lx = jj % TX;
+            lz = w < 7 ? w - 7 : TZ + w - 7;
+            ax = 2;
+        }
+        const int x = x0 + lx, z = z0 + lz;
+        R Qv[3] = {0, 0, 0};
+        if (inside(x, z)) {
+            R gs;
+            double gk;
+            pres_point<R, 2, NM, false>(A, make_pt(A, x, 0, z), at(x, z), Qv, gs, gk);
+        }
+        if (ax == 0) sQx[lz * T::QXW + lx + 7] = Qv[0];
+        else sQz[(lz + 7) * TX + lx] = Qv[2];
+    }
+    __syncthreads();
+
+    // g_d: the tile (full velocity adjoint along both axes), then the wings
+#pragma unroll
+    for (int k = 0; k < T::NI; ++k) {
+        const int j = tid + k * kAdjThreads, lx = j % TX, lz = j / TX, x = x0 + lx, z = z0 + lz;
+        R gx = 0, gz = 0;
+        if (inside(x, z)) {
+            const Pt<R> P = make_pt(A, x, 0, z);
+            gx = vel_point<R, NM, true, 0>(A, P, at(x, z), dplus_s(A, &sQx[lz * T::QXW + lx + 7], 1), gsum[k]);
+            gz = vel_point<R, NM, true, 2>(A, P, at(x, z), dplus_s(A, &sQz[(lz + 7) * TX + lx], TX), gsum[k]);
+        }
+        sGx[lz * T::GXW + lx + 4] = gx;
+        sGz[(lz + 4) * TX + lx] = gz;
+    }
+    for (int j = tid; j < 7 * (TZ + TX); j += kAdjThreads) {
+        int lx, lz, ax;
+        if (j < 7 * TZ) {    // g_x: 4 points before and 3 after each tile row
+            const int w = j % 7;
+            lz = j / 7;
+            lx = w < 4 ? w - 4 : TX + w - 4;
+            ax = 0;
+        } else {             // g_z: 4 rows above and 3 below the tile
+            const int jj = j - 7 * TZ, w = jj / TX;
+            lx = jj % TX;
+            lz = w < 4 ? w - 4 : TZ + w - 4;
+            ax = 2;
+        }
+        const int x = x0 + lx, z = z0 + lz;
+        R g = 0, unused = 0;
+        if (inside(x, z)) {
+            const Pt<R> P = make_pt(A, x, 0, z);
+            g = ax == 0 ? vel_point<R, NM, false, 0>(A, P, at(x, z), dplus_s(A, &sQx[lz * T::QXW + lx + 7], 1), unused)
+                        : vel_point<R, NM, false, 2>(A, P, at(x, z), dplus_s(A, &sQz[(lz + 7) * TX + lx], TX), unused);
+        }
+        if (ax == 0) sGx[lz * T::GXW + lx + 4] = g;
+        else sGz[(lz + 4) * TX + lx] = g;
+    }
+    __syncthreads();
+
+    // p: the backward differences of g_d on the tile
+#pragma unroll
+    for (int k = 0; k < T::NI; ++k) {
+        const int j = tid + k * kAdjThreads, lx = j % TX, lz = j / TX, x = x0 + lx, z = z0 + lz;
+        if (!inside(x, z)) continue;
+        const R s = dminus_s(A, &sGx[lz * T::GXW + lx + 4], 1) + dminus_s(A, &sGz[(lz + 4) * TX + lx], TX);
+        const long long i = at(x, z);
+        A.out.lp[i] = __ldg(A.in.lp + i) - s;
+        A.gs[i] += double(gsum[k]);
+    }
+}
+
+constexpr int kAdjTX = FWGB_ADJ_TX, kAdjTZ = FWGB_ADJ_TZ;
+
+template <typename R, int NM>
+cudaError_t launch_step2_n(const AdjArgs<R> &A, cudaStream_t s, bool setup)
+{
+    using T = AdjTile<kAdjTX, kAdjTZ>;
+    const size_t smem = (size_t)T::elems * sizeof(R);
+    if (setup) return cudaFuncSetAttribute(k_adj_step2<R, NM, kAdjTX, kAdjTZ>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const dim3 grid((unsigned)((A.nx + kAdjTX - 1) / kAdjTX), (unsigned)((A.nz + kAdjTZ - 1) / kAdjTZ));
+    k_adj_step2<R, NM, kAdjTX, kAdjTZ><<<grid, kAdjThreads, smem, s>>>(A);
+    return cudaGetLastError();
+}
+
+// the reverse step's kernels: one in 2D, three in 3D; instantiated per
+// dimension and number of mechanisms (their loops unroll).  With setup, only
+// the one-kernel form's shared-memory opt-in.
+template <typename R, int NM>
+cudaError_t launch_reverse_n(const AdjArgs<R> &A, int ndim, dim3 grid, cudaStream_t s, bool setup)
+{
+    if (ndim == 2) return launch_step2_n<R, NM>(A, s, setup);
+    if (setup) return cudaSuccess;
+    k_adj_pres<R, 3, NM><<<grid, 256, 0, s>>>(A);
+    k_adj_vel<R, 3, NM><<<grid, 256, 0, s>>>(A);
+    k_adj_p<R, 3, NM><<<grid, 256, 0, s>>>(A);
+    return cudaGetLastError();
 }
 
 template <typename R>
-void launch_reverse(const AdjArgs<R> &A, int ndim, int nmech, dim3 grid, cudaStream_t s)
+cudaError_t launch_reverse(const AdjArgs<R> &A, int ndim, int nmech, dim3 grid, cudaStream_t s, bool setup = false)
 {
-    if (ndim == 2) {
-        switch (nmech) {
-        case 1: launch_reverse_dn<R, 2, 1>(A, grid, s); break;
-        case 2: launch_reverse_dn<R, 2, 2>(A, grid, s); break;
-        case 3: launch_reverse_dn<R, 2, 3>(A, grid, s); break;
-        default: launch_reverse_dn<R, 2, 4>(A, grid, s); break;
-        }
-    } else {
-        switch (nmech) {
-        case 1: launch_reverse_dn<R, 3, 1>(A, grid, s); break;
-        case 2: launch_reverse_dn<R, 3, 2>(A, grid, s); break;
-        case 3: launch_reverse_dn<R, 3, 3>(A, grid, s); break;
-        default: launch_reverse_dn<R, 3, 4>(A, grid, s); break;
-        }
+    switch (nmech) {
+    case 1: return launch_reverse_n<R, 1>(A, ndim, grid, s, setup);
+    case 2: return launch_reverse_n<R, 2>(A, ndim, grid, s, setup);
+    case 3: return launch_reverse_n<R, 3>(A, ndim, grid, s, setup);
+    default: return launch_reverse_n<R, 4>(A, ndim, grid, s, setup);
     }
 }
 
@@ -359,6 +650,25 @@ void dab(double d, double al, double ka, double dt, double &da, double &db)
     da = d * al * (b - 1.0) / ((d + ka * al) * (d + ka * al)) + d / (ka * (d + ka * al)) * db;
 }
 
+// The recomputation's side stream and the events between it and the caller's
+// stream; on every way out, both streams finish before the buffers go.
+struct SideStream {
+    cudaStream_t main = nullptr, side = nullptr;
+    std::vector<cudaEvent_t> ev;
+    SideStream() = default;
+    SideStream(const SideStream &) = delete;
+    SideStream &operator=(const SideStream &) = delete;
+    ~SideStream()
+    {
+        if (side) {
+            cudaStreamSynchronize(side);
+            cudaStreamDestroy(side);
+        }
+        if (main) cudaStreamSynchronize(main);
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
+};
+
 template <typename R>
 int gradient_impl(fw_medium *m, int n_steps, int K, const void *G, const void *alpha0, void *grad_c, void *grad_a,
                   int as_f64, cudaStream_t s)
@@ -370,16 +680,25 @@ int gradient_impl(fw_medium *m, int n_steps, int K, const void *G, const void *a
     char *slab = static_cast<char *>(m->slab);
     auto off = [slab](const void *p) { return (size_t)(static_cast<const char *>(p) - slab); };
 
-    Buf lam(SB), ck((size_t)n_ck * SB), seg((size_t)(seg_len + 1) * SB), fin(SB);
-    Buf scratch(6 * vol * sizeof(R)), gacc(2 * vol * sizeof(double)), uacc(2 * n_user * sizeof(double));
+    // 2D: one kernel per reverse step, reading the adjoint state from one of a
+    // pair of buffers and writing the other; 3D: three kernels in place, with
+    // the adjoints of q_d and g_d in global scratch.
+    const bool one_kernel = m->ndim == 2;
+    // segment images: the states after steps k0 .. k1-2 of a segment (the state
+    // before it is its checkpoint, the state after it the next checkpoint)
+    Buf lam(SB), lam2(one_kernel ? SB : 0), ck((size_t)n_ck * SB), fin(SB);
+    Buf seg0((size_t)std::max(seg_len - 1, 1) * SB), seg1(n_ck > 1 ? (size_t)std::max(seg_len - 1, 1) * SB : 0);
+    Buf scratch(one_kernel ? 0 : 6 * vol * sizeof(R)), gacc(2 * vol * sizeof(double)),
+        uacc(2 * n_user * sizeof(double));
     const size_t nG = (size_t)m->n_rcv * m->n_rec;
     Buf dG(nG * sizeof(R)), dA0(alpha0 ? n_user * (as_f64 ? 8 : 4) : 0);
     Buf dlut((size_t)m->n_classes * kDStride * sizeof(R));
-    if (!lam.p || !ck.p || !seg.p || !fin.p || !scratch.p || !gacc.p || !uacc.p || (nG && !dG.p) ||
-        (alpha0 && !dA0.p) || !dlut.p)
+    if (!lam.p || (one_kernel && !lam2.p) || !ck.p || !seg0.p || (n_ck > 1 && !seg1.p) || !fin.p || (!one_kernel && !scratch.p) || !gacc.p ||
+        !uacc.p || (nG && !dG.p) || (alpha0 && !dA0.p) || !dlut.p)
         return FW_ERR_NOMEM;
     ADJ_CK(cudaMemsetAsync(lam.p, 0, SB, s));
-    ADJ_CK(cudaMemsetAsync(scratch.p, 0, 6 * vol * sizeof(R), s));
+    if (one_kernel) ADJ_CK(cudaMemsetAsync(lam2.p, 0, SB, s));
+    else ADJ_CK(cudaMemsetAsync(scratch.p, 0, 6 * vol * sizeof(R), s));
     ADJ_CK(cudaMemsetAsync(gacc.p, 0, 2 * vol * sizeof(double), s));
     ADJ_CK(cudaMemsetAsync(uacc.p, 0, 2 * n_user * sizeof(double), s));
     // receiver weights in the field type
@@ -439,24 +758,33 @@ int gradient_impl(fw_medium *m, int n_steps, int K, const void *G, const void *a
     A.dt = R(m->dt);
     A.wabs = m->wabs;
     A.inv_lr = m->wabs > 0 ? R(1) / R(m->g.transition > 0 ? m->g.transition : 0.5 * m->g.pml) : R(0);
-    char *L = static_cast<char *>(lam.p);
-    A.lp = reinterpret_cast<R *>(L + off(m->p));
+    // the adjoint state's fields at the medium's offsets inside a state-sized buffer
+    auto state_in = [&](void *buf) {
+        char *L = static_cast<char *>(buf);
+        AdjState<R> S{};
+        S.lp = reinterpret_cast<R *>(L + off(m->p));
+        for (int ax = 0; ax < 3; ++ax) {
+            S.lv[ax] = m->v[ax] ? reinterpret_cast<R *>(L + off(m->v[ax])) : nullptr;
+            S.lpsi1p[ax] = m->psi1p[ax] ? reinterpret_cast<R *>(L + off(m->psi1p[ax])) : nullptr;
+            S.lpsi2p[ax] = m->psi2p[ax] ? reinterpret_cast<R *>(L + off(m->psi2p[ax])) : nullptr;
+            for (int k = 0; k < m->nmech; ++k)
+                S.lpsi1[k][ax] = m->psi1[k][ax] ? reinterpret_cast<R *>(L + off(m->psi1[k][ax])) : nullptr;
+        }
+        for (int k = 0; k < m->nmech; ++k) S.lpsi2[k] = reinterpret_cast<R *>(L + off(m->psi2[k]));
+        return S;
+    };
+    A.in = state_in(lam.p);
+    A.out = one_kernel ? state_in(lam2.p) : A.in;
     for (int ax = 0; ax < 3; ++ax) {
         A.ax_on[ax] = m->v[ax] != nullptr;
-        A.lv[ax] = m->v[ax] ? reinterpret_cast<R *>(L + off(m->v[ax])) : nullptr;
-        A.lpsi1p[ax] = m->psi1p[ax] ? reinterpret_cast<R *>(L + off(m->psi1p[ax])) : nullptr;
-        A.lpsi2p[ax] = m->psi2p[ax] ? reinterpret_cast<R *>(L + off(m->psi2p[ax])) : nullptr;
-        for (int k = 0; k < m->nmech; ++k)
-            A.lpsi1[k][ax] = m->psi1[k][ax] ? reinterpret_cast<R *>(L + off(m->psi1[k][ax])) : nullptr;
         const bool layer = m->psi1p[ax] != nullptr;
         A.pdh[ax] = layer ? static_cast<const R *>(m->prof[ax][0]) : nullptr;
         A.pah[ax] = layer ? static_cast<const R *>(m->prof[ax][1]) : nullptr;
         A.pdi[ax] = layer ? static_cast<const R *>(m->prof[ax][2]) : nullptr;
         A.pai[ax] = layer ? static_cast<const R *>(m->prof[ax][3]) : nullptr;
-        A.Q[ax] = static_cast<R *>(scratch.p) + ax * vol;
-        A.Gd[ax] = static_cast<R *>(scratch.p) + (3 + ax) * vol;
+        A.Q[ax] = one_kernel ? nullptr : static_cast<R *>(scratch.p) + ax * vol;
+        A.Gd[ax] = one_kernel ? nullptr : static_cast<R *>(scratch.p) + (3 + ax) * vol;
     }
-    for (int k = 0; k < m->nmech; ++k) A.lpsi2[k] = reinterpret_cast<R *>(L + off(m->psi2[k]));
     A.kdt = static_cast<const R *>(m->kdt);
     A.rho = static_cast<const R *>(m->rho);
     A.cls = m->cls;
@@ -464,31 +792,75 @@ int gradient_impl(fw_medium *m, int n_steps, int K, const void *G, const void *a
     A.dlut = static_cast<const R *>(dlut.p);
     A.gk = static_cast<double *>(gacc.p);
     A.gs = static_cast<double *>(gacc.p) + vol;
-    auto image = [&](int k) { return static_cast<const char *>(seg.p) + (size_t)k * SB; };
     const dim3 pgrid((unsigned)((m->NX + 255) / 256), (unsigned)m->NY, (unsigned)m->NZ);   // one thread per point
     const double inv_dxd = 1.0 / std::pow(m->dx, m->ndim);
+    ADJ_CK(launch_reverse<R>(A, m->ndim, m->nmech, pgrid, s, true));
 
     // ---- reverse sweep, one checkpoint segment at a time ----
+    // The recomputation of segment si - 1 (a side stream, into the other of two
+    // image buffers) runs beside the adjoint of segment si: the adjoint reads
+    // only the images and the medium's maps, never the medium's state.
+    SideStream ss;
+    ss.main = s;
+    ADJ_CK(cudaStreamCreateWithFlags(&ss.side, cudaStreamNonBlocking));
+    cudaEvent_t ev_start, rec_done[2], rev_done[2], side_done;
+    for (cudaEvent_t *e : {&ev_start, &rec_done[0], &rec_done[1], &rev_done[0], &rev_done[1], &side_done}) {
+        ADJ_CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+        ss.ev.push_back(*e);
+    }
+    bool rev_recorded[2] = {false, false};
+    char *segs[2] = {static_cast<char *>(seg0.p), static_cast<char *>(seg1.p)};
+    // images after steps k0 .. k1-2 of segment si into segs[si & 1]
+    auto recompute = [&](int si) -> int {
+        const int k0 = si * K, k1 = std::min(n_steps, k0 + K);
+        if (k1 - k0 <= 1) return FW_OK;
+        if (cudaMemcpyAsync(slab, static_cast<const char *>(ck.p) + (size_t)si * SB, SB, cudaMemcpyDeviceToDevice,
+                            ss.side) != cudaSuccess)
+            return FW_ERR_CUDA;
+        m->step = it0 + k0;
+        for (int k = k0; k < k1 - 1; ++k) {
+            int rc = fw_run(m, 1, ss.side);
+            if (rc) return rc;
+            if (cudaMemcpyAsync(segs[si & 1] + (size_t)(k - k0) * SB, slab, SB, cudaMemcpyDeviceToDevice,
+                                ss.side) != cudaSuccess)
+                return FW_ERR_CUDA;
+        }
+        return FW_OK;
+    };
+    ADJ_CK(cudaEventRecord(ev_start, s));   // the forward run and the checkpoints
+    ADJ_CK(cudaStreamWaitEvent(ss.side, ev_start, 0));
+    {
+        int rc = recompute(n_ck - 1);
+        if (rc) return rc;
+    }
+    ADJ_CK(cudaEventRecord(rec_done[(n_ck - 1) & 1], ss.side));
     for (int si = n_ck - 1; si >= 0; --si) {
         const int k0 = si * K, k1 = std::min(n_steps, k0 + K);
-        ADJ_CK(cudaMemcpyAsync(slab, static_cast<char *>(ck.p) + (size_t)si * SB, SB, cudaMemcpyDeviceToDevice, s));
-        m->step = it0 + k0;
-        ADJ_CK(cudaMemcpyAsync(seg.p, slab, SB, cudaMemcpyDeviceToDevice, s));
-        for (int k = k0; k < k1; ++k) {
-            int rc = fw_run(m, 1, s);
+        ADJ_CK(cudaStreamWaitEvent(s, rec_done[si & 1], 0));
+        if (si >= 1) {
+            // segs[(si - 1) & 1] was last read by the adjoint of segment si + 1
+            if (rev_recorded[(si + 1) & 1]) ADJ_CK(cudaStreamWaitEvent(ss.side, rev_done[(si + 1) & 1], 0));
+            int rc = recompute(si - 1);
             if (rc) return rc;
-            ADJ_CK(cudaMemcpyAsync(static_cast<char *>(seg.p) + (size_t)(k - k0 + 1) * SB, slab, SB,
-                                   cudaMemcpyDeviceToDevice, s));
+            ADJ_CK(cudaEventRecord(rec_done[(si - 1) & 1], ss.side));
         }
+        const char *ck_si = static_cast<const char *>(ck.p) + (size_t)si * SB;
+        // image j of the segment: the state after step k0 + j - 1
+        auto image = [&](int j) -> const char * {
+            if (j == 0) return ck_si;
+            if (j == k1 - k0) return si + 1 < n_ck ? ck_si + SB : static_cast<const char *>(fin.p);
+            return segs[si & 1] + (size_t)(j - 1) * SB;
+        };
         for (int k = k1 - 1; k >= k0; --k) {
             const long long it = it0 + k;
             if (m->n_rcv > 0 && it % m->decim == 0 && it / m->decim < m->n_rec)
-                k_adj_rcv<R><<<(m->n_rcv + 255) / 256, 256, 0, s>>>(A.lp, m->rcv_idx, static_cast<const R *>(dG.p),
-                                                                   m->n_rcv, m->n_rec, (int)(it / m->decim));
+                k_adj_rcv<R><<<(m->n_rcv + 255) / 256, 256, 0, s>>>(A.in.lp, m->rcv_idx,
+                                                                   static_cast<const R *>(dG.p), m->n_rcv, m->n_rec,
+                                                                   (int)(it / m->decim));
             if (m->n_src > 0 && it < m->wave_len)
-                k_adj_src<R><<<(m->n_src + 255) / 256, 256, 0, s>>>(A.lp, m->src_idx, static_cast<const R *>(m->waves),
-                                                                   m->wave_of, m->wave_len, (int)it, m->n_src,
-                                                                   inv_dxd, A.gk);
+                k_adj_src<R><<<(m->n_src + 255) / 256, 256, 0, s>>>(A.in.lp, m->src_idx,
+                                                                   static_cast<const R *>(m->waves), m->wave_of,
+                                                                   m->wave_len, (int)it, m->n_src, inv_dxd, A.gk);
             const char *F = image(k - k0), *F1 = image(k - k0 + 1);
             A.fp = reinterpret_cast<const R *>(F + off(m->p));
             for (int ax = 0; ax < 3; ++ax) {
@@ -498,10 +870,15 @@ int gradient_impl(fw_medium *m, int n_steps, int K, const void *G, const void *a
                     A.fpsi1[q][ax] = m->psi1[q][ax] ? reinterpret_cast<const R *>(F + off(m->psi1[q][ax])) : nullptr;
             }
             for (int q = 0; q < m->nmech; ++q) A.fpsi2[q] = reinterpret_cast<const R *>(F + off(m->psi2[q]));
-            launch_reverse<R>(A, m->ndim, m->nmech, pgrid, s);
+            ADJ_CK(launch_reverse<R>(A, m->ndim, m->nmech, pgrid, s));
+            if (one_kernel) std::swap(A.in, A.out);
         }
+        ADJ_CK(cudaEventRecord(rev_done[si & 1], s));
+        rev_recorded[si & 1] = true;
         ADJ_CK(cudaGetLastError());
     }
+    ADJ_CK(cudaEventRecord(side_done, ss.side));
+    ADJ_CK(cudaStreamWaitEvent(s, side_done, 0));
     // leave the medium at the end of the forward run
     ADJ_CK(cudaMemcpyAsync(slab, fin.p, SB, cudaMemcpyDeviceToDevice, s));
     m->step = it0 + n_steps;

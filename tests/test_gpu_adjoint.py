@@ -74,13 +74,17 @@ def _oracle_grad(P, checkpoint=50):
                            checkpoint=checkpoint)
 
 
-@pytest.mark.parametrize("shape", [(48, 41), (20, 18, 23)])
+@pytest.mark.parametrize("shape", [(48, 41), (100, 150), (20, 18, 23)])
 def test_gradient_matches_oracle(fw, shape):
     """Random class map (two lossy classes and a lossless one), absorbing
     layer, point source, receiver line; FP64 and FP32 kernels against the
     oracle's FP64 discrete adjoint; the run leaves the medium at the end of
-    the window with the traces of a plain run."""
-    P = _problem(shape, seed=len(shape), n_steps=160 if len(shape) == 2 else 90, pml=6 if len(shape) == 2 else 3)
+    the window with the traces of a plain run.  The 100 x 150 grid spans
+    several tiles of the 2D reverse-step kernel along both axes, with ragged
+    last tiles (320 steps: the direct wave reaches its receivers 83 cells
+    from the source)."""
+    n_steps = (320 if shape[0] == 100 else 160) if len(shape) == 2 else 90
+    P = _problem(shape, seed=len(shape), n_steps=n_steps, pml=6 if len(shape) == 2 else 3)
     orc = _oracle_grad(P)
     assert np.abs(orc["grad_c"]).max() > 0 and np.abs(orc["grad_alpha0"]).max() > 0
     for storage, tol in (("f64", 1e-12), ("f32", 1e-4)):
@@ -105,7 +109,7 @@ def test_c5_gradient_vs_finite_differences_and_oracle(fw):
     """Adjoint workload: 1024^2 Voronoi medium (6 classes, N = 3), 64
     receivers, 3000 steps, checkpoint every 100; misfit 1/2 |traces - d_obs|^2
     with d_obs from the perturbed medium (c +1 %, alpha0 +20 % in a Gaussian
-    blob).  The FP32 and FP64 gradients at 32 seeded voxels against central
+    blob; the alpha0 factor on every d of the class, in 64 levels).  The FP32 and FP64 gradients at 32 seeded voxels against central
     differences of the FP64 forward run (c: the voxel's c; alpha0: the voxel
     gets its own class with every d scaled, the reading of fw_gradient)."""
     import time
@@ -123,9 +127,21 @@ def test_c5_gradient_vs_finite_differences_and_oracle(fw):
         m.set_receivers(spec.rcv_mask, spec.n_steps)
         return m
 
-    # observed data: the perturbed medium's own classes (alpha0 +20 % as a d scale in the blob is
-    # not representable by classes, so the observed data use the perturbed c only)
-    mt = medium(true.maps["c"], "f64")
+    # observed data: the perturbed medium, c +1 % and alpha0 +20 % in the blob.  The alpha0 factor
+    # s(x) = alpha0_true(x) / alpha0_class scales every d of the voxel's class (the reading of
+    # fw_gradient); s is quantised to 64 levels across its range, one class per (class, level).
+    levels = 64
+    s_true = np.where(a0c[cls] > 0, true.maps["alpha0"].astype(np.float64) / np.maximum(a0c[cls], 1e-30), 1.0)
+    lev = np.clip(np.rint((s_true - 1.0) / 0.2 * (levels - 1)), 0, levels - 1).astype(np.int64)
+    assert lev.max() >= levels - 8   # the blob's centre reaches the top levels
+    blob_classes = []
+    for q in params:
+        for lv in range(levels):
+            sc = 1.0 + 0.2 * lv / (levels - 1)
+            blob_classes.append(fw.relax_params(q.kappa1, q.kappa2, [x * sc for x in q.d1], q.alpha1,
+                                                [x * sc for x in q.d2], q.alpha2))
+    mt = medium(true.maps["c"], "f64", cls_map=(cls.astype(np.int64) * levels + lev).astype(np.uint16),
+                classes=blob_classes)
     mt.run(spec.n_steps)
     d_obs = mt.receivers(f64=True)
     mt.close()
