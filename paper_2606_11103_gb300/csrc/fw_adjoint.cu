@@ -41,6 +41,8 @@ namespace fwgb {
 void *device_alloc(size_t bytes);
 void device_free(void *p);
 size_t state_image_bytes(const fw_medium *m);
+cudaError_t image_step_f32(const fw_medium *m, const StepImages &im, const int *zero, int it, cudaStream_t s);
+cudaError_t image_step_f64(const fw_medium *m, const StepImages &im, const int *zero, int it, cudaStream_t s);
 }  // namespace fwgb
 
 using namespace fwgb;
@@ -307,19 +309,31 @@ __global__ void k_adj_p(const AdjArgs<R> A)
     A.out.lp[i] = A.in.lp[i] - s;
 }
 
+// Transpose of the step's injection and recording (k_io), in one launch:
+// threads [0, n_src) add the adjoint of the receiver on the source's cell
+// (if any and if col >= 0) to the pressure adjoint there and take the
+// source-gain gradient of step it (it < wave_len) from it; threads
+// [n_src, n_src + n_rcv) add the adjoints of the other receivers (col >= 0).
 template <typename R>
-__global__ void k_adj_rcv(R *lp, const long long *idx, const R *G, int n_rcv, int n_col, int col)
+__global__ void k_adj_io(R *lp, const long long *src_idx, const R *waves, const int *wave_of, int wave_len, int it,
+                         int n_src, const int *src_rcv, const long long *rcv_idx, const int *rcv_src, const R *G,
+                         int n_rcv, int n_col, int col, double inv_dxd, double *gk)
 {
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n_rcv; r += gridDim.x * blockDim.x)
-        lp[idx[r]] += G[(size_t)r * n_col + col];
-}
-
-template <typename R>
-__global__ void k_adj_src(const R *lp, const long long *idx, const R *waves, const int *wave_of, int wave_len,
-                          int it, int n_src, double inv_dxd, double *gk)
-{
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n_src; s += gridDim.x * blockDim.x)
-        gk[idx[s]] += double(waves[(size_t)wave_of[s] * wave_len + it]) * double(lp[idx[s]]) * inv_dxd;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n_src) {
+        const long long k = src_idx[t];
+        const int r = col >= 0 ? src_rcv[t] : -1;
+        R l = lp[k];
+        if (r >= 0) {
+            l += G[(size_t)r * n_col + col];
+            lp[k] = l;
+        }
+        if (it < wave_len) gk[k] += double(waves[(size_t)wave_of[t] * wave_len + it]) * double(l) * inv_dxd;
+    } else if (col >= 0 && t < n_src + n_rcv) {
+        const int r = t - n_src;
+        if (rcv_src[r] >= 0) return;     // added by the thread of the source on its cell
+        lp[rcv_idx[r]] += G[(size_t)r * n_col + col];
+    }
 }
 
 // internal gradients -> the user's grid (transpose of the layer inheritance)
@@ -391,11 +405,115 @@ constexpr int kAdjThreads = FWGB_ADJ_THREADS;
 template <int TX, int TZ> struct AdjTile {
     static constexpr int QXW = TX + 14, QZH = TZ + 14;   // q_x rows, q_z columns
     static constexpr int GXW = TX + 7, GZH = TZ + 7;     // g_x rows, g_z columns
+    static constexpr int FPW = TX + 7, FPH = TZ + 7;     // forward p: columns x0-3 .., rows z0-3 ..
     static constexpr int n_qx = TZ * QXW, n_qz = QZH * TX, n_gx = TZ * GXW, n_gz = GZH * TX;
-    static constexpr int elems = n_qx + n_qz + n_gx + n_gz;
+    static constexpr int n_fp = FPH * FPW, n_v0 = TZ * (TX + 7), n_v2 = (TZ + 7) * TX;
+    static constexpr int elems = n_qx + n_qz + n_gx + n_gz + n_fp + n_v0 + n_v2;
     static constexpr int NI = TX * TZ / kAdjThreads;     // tile points per thread
     static_assert(TX * TZ % kAdjThreads == 0, "tile points split evenly over the threads");
 };
+
+// ---- one-kernel form (2D) ----
+// tissue-mechanism strength of the cell (x, z) (cell_ramp of a 2D grid)
+template <typename R>
+__device__ __forceinline__ R ramp2(const AdjArgs<R> &A, int x, int z)
+{
+    const R s = fmax(layer_depth<R>(x, A.nx, A.wabs), layer_depth<R>(z, A.nz, A.wabs));
+    return ramp_of(s, A.inv_lr);
+}
+
+// Pressure adjoint at an in-grid point i = (x, z) of class table t / dtb and
+// tissue strength r: the adjoints of q_x and q_z (Qx, Qz; the halo needs one
+// of them, ONLY = 0 or 2).  FULL: qx, qz are the forward D- differences of
+// v after the step at the point; takes this step's gradient terms (gs, gk)
+// and writes the memory variables before the step.  PLAIN: no absorbing
+// layer within reach of the tile (r = 1, no layer memory).
+template <typename R, int NM, bool FULL, bool PLAIN, int ONLY = -1>
+__device__ __forceinline__ void pres2(const AdjArgs<R> &A, int x, int z, long long i, const R *t, const R *dtb, R r,
+                                      R qx, R qz, R &Qx, R &Qz, R &gs, double &gk)
+{
+    const R div = qx + qz;
+    const R lp = __ldg(A.in.lp + i);
+    const R lst = -__ldg(A.kdt + i) * lp;
+    const R ce = PLAIN ? __ldg(t + 3) : __ldg(t + 3) + (r - R(1)) * __ldg(t + kLutDk + 1);
+    R stp = div * ce;
+    R ldiv = ce * lst;
+    gs = 0;
+#pragma unroll
+    for (int m = 0; m < NM; ++m) {
+        const R ln = __ldg(A.in.lpsi2[m] + i);
+        ldiv += (PLAIN ? R(1) : r) * __ldg(t + kLutA2 + m) * ln;
+        if (FULL) {
+            const R old = __ldg(A.fpsi2[m] + i);
+            const R h = __ldg(t + kLutH2 + m);
+            stp += h * old;
+            gs += (__ldg(dtb + 12 + m) * old + (PLAIN ? R(1) : r) * __ldg(dtb + 8 + m) * div) * (ln + R(0.5) * lst);
+            A.out.lpsi2[m][i] = __ldg(t + kLutB2 + m) * ln + h * lst;
+        }
+    }
+    Qx = Qz = ldiv;
+    if (!PLAIN) {
+#pragma unroll
+        for (int ax = 0; ax < 3; ax += 2) {
+            if (ONLY >= 0 && ax != ONLY) continue;
+            if (!A.pdi[ax]) continue;
+            const int c = ax == 0 ? x : z;
+            const R d = __ldg(A.pdi[ax] + c);
+            if (d > R(0)) {
+                R a, b;
+                pml_ab(d, __ldg(A.pai[ax] + c), __ldg(t + 1), A.dt, a, b);
+                const R ln = __ldg(A.in.lpsi2p[ax] + i);
+                (ax == 0 ? Qx : Qz) += a * (ln + R(0.5) * lst);
+                if (FULL) {
+                    const R old = __ldg(A.fpsi2p[ax] + i);
+                    stp += R(0.5) * (R(1) + b) * old + R(0.5) * a * (ax == 0 ? qx : qz);
+                    A.out.lpsi2p[ax][i] = b * ln + R(0.5) * (R(1) + b) * lst;
+                }
+            }
+        }
+    }
+    gk = FULL ? double(-stp * lp) : 0.0;
+}
+
+// Velocity adjoint along axis ax (0 or 2) at an in-grid point i, coordinate c
+// of n along ax, stride st: given dq = D+ of the adjoint of q_ax there,
+// returns the adjoint of g_ax.  FULL: g is the forward D+ difference of p
+// before the step; adds the gradient terms to gs and writes v_ax and the
+// memory variables before the step.
+template <typename R, int NM, bool FULL, bool PLAIN, int ax>
+__device__ __forceinline__ R vel2(const AdjArgs<R> &A, int c, int n, long long st, long long i, const R *t,
+                                  const R *dtb, R r, R dq, R g, R &gs)
+{
+    const R own = __ldg(A.rho + i);
+    const R ce = PLAIN ? __ldg(t + 2) : __ldg(t + 2) + (r - R(1)) * __ldg(t + kLutDk);
+    const R lv = __ldg(A.in.lv[ax] + i) - dq;
+    const R nxt = (c + 1 < n) ? __ldg(A.rho + i + st) : own;
+    const R dtr = R(2) * A.dt * fw_rcp(own + nxt);
+    const R lst = -dtr * lv;
+    R lg = ce * lst;
+#pragma unroll
+    for (int m = 0; m < NM; ++m) {
+        const R ln = __ldg(A.in.lpsi1[m][ax] + i);
+        lg += (PLAIN ? R(1) : r) * __ldg(t + kLutA1 + m) * ln;
+        if (FULL) {
+            const R old = __ldg(A.fpsi1[m][ax] + i);
+            gs += (__ldg(dtb + 4 + m) * old + (PLAIN ? R(1) : r) * __ldg(dtb + m) * g) * (ln + R(0.5) * lst);
+            A.out.lpsi1[m][ax][i] = __ldg(t + kLutB1 + m) * ln + __ldg(t + kLutH1 + m) * lst;
+        }
+    }
+    if (!PLAIN && A.pdh[ax]) {
+        const R d = __ldg(A.pdh[ax] + c);
+        if (d > R(0)) {
+            R a, b;
+            pml_ab(d, __ldg(A.pah[ax] + c), __ldg(t), A.dt, a, b);
+            const R ln = __ldg(A.in.lpsi1p[ax] + i);
+            lg += a * (ln + R(0.5) * lst);
+            if (FULL) A.out.lpsi1p[ax][i] = b * ln + R(0.5) * (R(1) + b) * lst;
+        }
+    }
+    if (FULL) A.out.lv[ax][i] = lv;
+    return lg;
+}
 
 #ifndef FWGB_ADJ_PREFETCH
 #define FWGB_ADJ_PREFETCH 2   // 0: none, 1: both sides at the start, 2: velocity side after the tile's q_d
@@ -476,59 +594,94 @@ __device__ __forceinline__ void prefetch_side(const AdjArgs<R> &A, int side, int
     }
 }
 
-template <typename R, int NM, int TX, int TZ>
-__global__ void __launch_bounds__(kAdjThreads) k_adj_step2(const AdjArgs<R> A)
+// The reverse step on one TX x TZ tile: the pressure adjoint on the tile and
+// on the q_d halo (7 points either side along d), the velocity adjoint on the
+// tile and on the g_d halo (4 before, 3 after), then the update of the
+// pressure adjoint on the tile.  The forward fields whose differences the
+// step takes (p before the step, v after it) are staged in shared memory
+// with their halos, zero beyond the grid.
+template <typename R, int NM, int TX, int TZ, bool PLAIN>
+__device__ __forceinline__ void step2_tile(const AdjArgs<R> &A, unsigned char *smem, int x0, int z0)
 {
     using T = AdjTile<TX, TZ>;
-    extern __shared__ __align__(16) unsigned char adj_smem[];
-    R *sQx = reinterpret_cast<R *>(adj_smem);
+    R *sQx = reinterpret_cast<R *>(smem);
     R *sQz = sQx + T::n_qx;
     R *sGx = sQz + T::n_qz;
     R *sGz = sGx + T::n_gx;
-    const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ, tid = threadIdx.x;
+    R *sFP = sGz + T::n_gz;   // p before the step: rows z0-3 .. z0+TZ+3, columns x0-3 .. x0+TX+3
+    R *sV0 = sFP + T::n_fp;   // v_x after it: rows z0 .. z0+TZ-1, columns x0-4 .. x0+TX+2
+    R *sV2 = sV0 + T::n_v0;   // v_z after it: rows z0-4 .. z0+TZ+2, columns x0 .. x0+TX-1
+    const int tid = threadIdx.x;
     auto inside = [&](int x, int z) { return x >= 0 && x < A.nx && z >= 0 && z < A.nz; };
     auto at = [&](int x, int z) { return (long long)z * A.plane + x; };
-    R gsum[T::NI];
-    if (FWGB_ADJ_PREFETCH >= 1) prefetch_side<R, NM, TX, TZ>(A, 0, x0, z0);
-    if (FWGB_ADJ_PREFETCH == 1) prefetch_side<R, NM, TX, TZ>(A, 1, x0, z0);
+    auto tab = [&](int cl) { return A.lut + (size_t)cl * kLutStride; };
+    auto dtab = [&](int cl) { return A.dlut + (size_t)cl * kDStride; };
 
+    for (int j = tid; j < T::n_fp; j += kAdjThreads) {
+        const int x = x0 - 3 + j % T::FPW, z = z0 - 3 + j / T::FPW;
+        sFP[j] = inside(x, z) ? __ldg(A.fp + at(x, z)) : R(0);
+    }
+    for (int j = tid; j < T::n_v0; j += kAdjThreads) {
+        const int x = x0 - 4 + j % (TX + 7), z = z0 + j / (TX + 7);
+        sV0[j] = inside(x, z) ? __ldg(A.fv1[0] + at(x, z)) : R(0);
+    }
+    for (int j = tid; j < T::n_v2; j += kAdjThreads) {
+        const int x = x0 + j % TX, z = z0 - 4 + j / TX;
+        sV2[j] = inside(x, z) ? __ldg(A.fv1[2] + at(x, z)) : R(0);
+    }
+    __syncthreads();
+
+    R gsum[T::NI], rk[T::NI];
+    int clk[T::NI];
     // q_d: the tile (full pressure adjoint), then the wings
 #pragma unroll
     for (int k = 0; k < T::NI; ++k) {
         const int j = tid + k * kAdjThreads, lx = j % TX, lz = j / TX, x = x0 + lx, z = z0 + lz;
-        R Qv[3] = {0, 0, 0};
+        R Qx = 0, Qz = 0;
         gsum[k] = 0;
+        clk[k] = 0;
+        rk[k] = R(1);
         if (inside(x, z)) {
+            const long long i = at(x, z);
+            const int cl = __ldg(A.cls + i);
+            const R r = PLAIN ? R(1) : ramp2(A, x, z);
+            clk[k] = cl;
+            rk[k] = r;
+            const R qx = dminus_s(A, &sV0[lz * (TX + 7) + lx + 4], 1);
+            const R qz = dminus_s(A, &sV2[(lz + 4) * TX + lx], TX);
             double gk;
-            pres_point<R, 2, NM, true>(A, make_pt(A, x, 0, z), at(x, z), Qv, gsum[k], gk);
-            A.gk[at(x, z)] += gk;
+            pres2<R, NM, true, PLAIN>(A, x, z, i, tab(cl), dtab(cl), r, qx, qz, Qx, Qz, gsum[k], gk);
+            A.gk[i] += gk;
         }
-        sQx[lz * T::QXW + lx + 7] = Qv[0];
-        sQz[(lz + 7) * TX + lx] = Qv[2];
+        sQx[lz * T::QXW + lx + 7] = Qx;
+        sQz[(lz + 7) * TX + lx] = Qz;
     }
     if (FWGB_ADJ_PREFETCH == 2) prefetch_side<R, NM, TX, TZ>(A, 1, x0, z0);
     for (int j = tid; j < 14 * (TZ + TX); j += kAdjThreads) {
-        int lx, lz, ax;
-        if (j < 14 * TZ) {   // q_x: 7 points either side of each tile row
+        int lx, lz;
+        const bool along_x = j < 14 * TZ;
+        if (along_x) {       // q_x: 7 points either side of each tile row
             const int w = j % 14;
             lz = j / 14;
             lx = w < 7 ? w - 7 : TX + w - 7;
-            ax = 0;
         } else {             // q_z: 7 rows above and below the tile
             const int jj = j - 14 * TZ, w = jj / TX;
             lx = jj % TX;
             lz = w < 7 ? w - 7 : TZ + w - 7;
-            ax = 2;
         }
         const int x = x0 + lx, z = z0 + lz;
-        R Qv[3] = {0, 0, 0};
+        R Qx = 0, Qz = 0;
         if (inside(x, z)) {
+            const long long i = at(x, z);
+            const int cl = __ldg(A.cls + i);
+            const R r = PLAIN ? R(1) : ramp2(A, x, z);
             R gs;
             double gk;
-            pres_point<R, 2, NM, false>(A, make_pt(A, x, 0, z), at(x, z), Qv, gs, gk);
+            if (along_x) pres2<R, NM, false, PLAIN, 0>(A, x, z, i, tab(cl), dtab(cl), r, R(0), R(0), Qx, Qz, gs, gk);
+            else pres2<R, NM, false, PLAIN, 2>(A, x, z, i, tab(cl), dtab(cl), r, R(0), R(0), Qx, Qz, gs, gk);
         }
-        if (ax == 0) sQx[lz * T::QXW + lx + 7] = Qv[0];
-        else sQz[(lz + 7) * TX + lx] = Qv[2];
+        if (along_x) sQx[lz * T::QXW + lx + 7] = Qx;
+        else sQz[(lz + 7) * TX + lx] = Qz;
     }
     __syncthreads();
 
@@ -538,34 +691,41 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_step2(const AdjArgs<R> A)
         const int j = tid + k * kAdjThreads, lx = j % TX, lz = j / TX, x = x0 + lx, z = z0 + lz;
         R gx = 0, gz = 0;
         if (inside(x, z)) {
-            const Pt<R> P = make_pt(A, x, 0, z);
-            gx = vel_point<R, NM, true, 0>(A, P, at(x, z), dplus_s(A, &sQx[lz * T::QXW + lx + 7], 1), gsum[k]);
-            gz = vel_point<R, NM, true, 2>(A, P, at(x, z), dplus_s(A, &sQz[(lz + 7) * TX + lx], TX), gsum[k]);
+            const long long i = at(x, z);
+            const R *t = tab(clk[k]), *dtb = dtab(clk[k]);
+            const R *fp = &sFP[(lz + 3) * T::FPW + lx + 3];
+            gx = vel2<R, NM, true, PLAIN, 0>(A, x, A.nx, 1, i, t, dtb, rk[k], dplus_s(A, &sQx[lz * T::QXW + lx + 7], 1),
+                                             dplus_s(A, fp, 1), gsum[k]);
+            gz = vel2<R, NM, true, PLAIN, 2>(A, z, A.nz, A.plane, i, t, dtb, rk[k],
+                                             dplus_s(A, &sQz[(lz + 7) * TX + lx], TX), dplus_s(A, fp, T::FPW), gsum[k]);
         }
         sGx[lz * T::GXW + lx + 4] = gx;
         sGz[(lz + 4) * TX + lx] = gz;
     }
     for (int j = tid; j < 7 * (TZ + TX); j += kAdjThreads) {
-        int lx, lz, ax;
-        if (j < 7 * TZ) {    // g_x: 4 points before and 3 after each tile row
+        int lx, lz;
+        const bool along_x = j < 7 * TZ;
+        if (along_x) {       // g_x: 4 points before and 3 after each tile row
             const int w = j % 7;
             lz = j / 7;
             lx = w < 4 ? w - 4 : TX + w - 4;
-            ax = 0;
         } else {             // g_z: 4 rows above and 3 below the tile
             const int jj = j - 7 * TZ, w = jj / TX;
             lx = jj % TX;
             lz = w < 4 ? w - 4 : TZ + w - 4;
-            ax = 2;
         }
         const int x = x0 + lx, z = z0 + lz;
         R g = 0, unused = 0;
         if (inside(x, z)) {
-            const Pt<R> P = make_pt(A, x, 0, z);
-            g = ax == 0 ? vel_point<R, NM, false, 0>(A, P, at(x, z), dplus_s(A, &sQx[lz * T::QXW + lx + 7], 1), unused)
-                        : vel_point<R, NM, false, 2>(A, P, at(x, z), dplus_s(A, &sQz[(lz + 7) * TX + lx], TX), unused);
+            const long long i = at(x, z);
+            const int cl = __ldg(A.cls + i);
+            const R r = PLAIN ? R(1) : ramp2(A, x, z);
+            g = along_x ? vel2<R, NM, false, PLAIN, 0>(A, x, A.nx, 1, i, tab(cl), dtab(cl), r,
+                                                       dplus_s(A, &sQx[lz * T::QXW + lx + 7], 1), R(0), unused)
+                        : vel2<R, NM, false, PLAIN, 2>(A, z, A.nz, A.plane, i, tab(cl), dtab(cl), r,
+                                                       dplus_s(A, &sQz[(lz + 7) * TX + lx], TX), R(0), unused);
         }
-        if (ax == 0) sGx[lz * T::GXW + lx + 4] = g;
+        if (along_x) sGx[lz * T::GXW + lx + 4] = g;
         else sGz[(lz + 4) * TX + lx] = g;
     }
     __syncthreads();
@@ -580,6 +740,23 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_step2(const AdjArgs<R> A)
         A.out.lp[i] = __ldg(A.in.lp + i) - s;
         A.gs[i] += double(gsum[k]);
     }
+}
+
+// Tiles whose reads (the q_d halo reaches 7 cells, one more for the velocity
+// adjoint's neighbouring density) stay clear of the absorbing layer take the
+// PLAIN instance: no layer memory, tissue strength 1.
+template <typename R, int NM, int TX, int TZ>
+__global__ void __launch_bounds__(kAdjThreads, sizeof(R) == 4 ? 4 : 2) k_adj_step2(const AdjArgs<R> A)
+{
+    extern __shared__ __align__(16) unsigned char adj_smem[];
+    const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ;
+    if (FWGB_ADJ_PREFETCH >= 1) prefetch_side<R, NM, TX, TZ>(A, 0, x0, z0);
+    if (FWGB_ADJ_PREFETCH == 1) prefetch_side<R, NM, TX, TZ>(A, 1, x0, z0);
+    constexpr int h = 8;
+    const bool plain = A.wabs <= 0 || (x0 - h >= A.wabs && x0 + TX + h <= A.nx - A.wabs && z0 - h >= A.wabs &&
+                                       z0 + TZ + h <= A.nz - A.wabs);
+    if (plain) step2_tile<R, NM, TX, TZ, true>(A, adj_smem, x0, z0);
+    else step2_tile<R, NM, TX, TZ, false>(A, adj_smem, x0, z0);
 }
 
 constexpr int kAdjTX = FWGB_ADJ_TX, kAdjTZ = FWGB_ADJ_TZ;
@@ -692,10 +869,11 @@ int gradient_impl(fw_medium *m, int n_steps, int K, const void *G, const void *a
         uacc(2 * n_user * sizeof(double));
     const size_t nG = (size_t)m->n_rcv * m->n_rec;
     Buf dG(nG * sizeof(R)), dA0(alpha0 ? n_user * (as_f64 ? 8 : 4) : 0);
-    Buf dlut((size_t)m->n_classes * kDStride * sizeof(R));
+    Buf dlut((size_t)m->n_classes * kDStride * sizeof(R)), zero(256);   // zero: step counter of the image steps
     if (!lam.p || (one_kernel && !lam2.p) || !ck.p || !seg0.p || (n_ck > 1 && !seg1.p) || !fin.p || (!one_kernel && !scratch.p) || !gacc.p ||
-        !uacc.p || (nG && !dG.p) || (alpha0 && !dA0.p) || !dlut.p)
+        !uacc.p || (nG && !dG.p) || (alpha0 && !dA0.p) || !dlut.p || !zero.p)
         return FW_ERR_NOMEM;
+    ADJ_CK(cudaMemsetAsync(zero.p, 0, 256, s));
     ADJ_CK(cudaMemsetAsync(lam.p, 0, SB, s));
     if (one_kernel) ADJ_CK(cudaMemsetAsync(lam2.p, 0, SB, s));
     else ADJ_CK(cudaMemsetAsync(scratch.p, 0, 6 * vol * sizeof(R), s));
@@ -810,20 +988,19 @@ int gradient_impl(fw_medium *m, int n_steps, int K, const void *G, const void *a
     }
     bool rev_recorded[2] = {false, false};
     char *segs[2] = {static_cast<char *>(seg0.p), static_cast<char *>(seg1.p)};
-    // images after steps k0 .. k1-2 of segment si into segs[si & 1]
+    // images after steps k0 .. k1-2 of segment si into segs[si & 1]: each step
+    // reads the image before it (the checkpoint first) and writes the next
     auto recompute = [&](int si) -> int {
         const int k0 = si * K, k1 = std::min(n_steps, k0 + K);
-        if (k1 - k0 <= 1) return FW_OK;
-        if (cudaMemcpyAsync(slab, static_cast<const char *>(ck.p) + (size_t)si * SB, SB, cudaMemcpyDeviceToDevice,
-                            ss.side) != cudaSuccess)
-            return FW_ERR_CUDA;
-        m->step = it0 + k0;
+        const char *rd = static_cast<const char *>(ck.p) + (size_t)si * SB;
         for (int k = k0; k < k1 - 1; ++k) {
-            int rc = fw_run(m, 1, ss.side);
-            if (rc) return rc;
-            if (cudaMemcpyAsync(segs[si & 1] + (size_t)(k - k0) * SB, slab, SB, cudaMemcpyDeviceToDevice,
-                                ss.side) != cudaSuccess)
+            char *wr = segs[si & 1] + (size_t)(k - k0) * SB;
+            const StepImages im{rd, (long long)(wr - rd)};
+            const int itk = (int)(it0 + k);
+            if ((sizeof(R) == 8 ? image_step_f64(m, im, static_cast<const int *>(zero.p), itk, ss.side)
+                                : image_step_f32(m, im, static_cast<const int *>(zero.p), itk, ss.side)) != cudaSuccess)
                 return FW_ERR_CUDA;
+            rd = wr;
         }
         return FW_OK;
     };
@@ -853,14 +1030,14 @@ int gradient_impl(fw_medium *m, int n_steps, int K, const void *G, const void *a
         };
         for (int k = k1 - 1; k >= k0; --k) {
             const long long it = it0 + k;
-            if (m->n_rcv > 0 && it % m->decim == 0 && it / m->decim < m->n_rec)
-                k_adj_rcv<R><<<(m->n_rcv + 255) / 256, 256, 0, s>>>(A.in.lp, m->rcv_idx,
-                                                                   static_cast<const R *>(dG.p), m->n_rcv, m->n_rec,
-                                                                   (int)(it / m->decim));
-            if (m->n_src > 0 && it < m->wave_len)
-                k_adj_src<R><<<(m->n_src + 255) / 256, 256, 0, s>>>(A.in.lp, m->src_idx,
-                                                                   static_cast<const R *>(m->waves), m->wave_of,
-                                                                   m->wave_len, (int)it, m->n_src, inv_dxd, A.gk);
+            const int col = (m->n_rcv > 0 && it % m->decim == 0 && it / m->decim < m->n_rec) ? (int)(it / m->decim) : -1;
+            if (col >= 0 || (m->n_src > 0 && it < m->wave_len)) {
+                const int n_io = m->n_src + (col >= 0 ? m->n_rcv : 0);
+                k_adj_io<R><<<(n_io + 255) / 256, 256, 0, s>>>(A.in.lp, m->src_idx, static_cast<const R *>(m->waves),
+                                                               m->wave_of, m->wave_len, (int)it, m->n_src, m->src_rcv,
+                                                               m->rcv_idx, m->rcv_src, static_cast<const R *>(dG.p),
+                                                               m->n_rcv, m->n_rec, col, inv_dxd, A.gk);
+            }
             const char *F = image(k - k0), *F1 = image(k - k0 + 1);
             A.fp = reinterpret_cast<const R *>(F + off(m->p));
             for (int ax = 0; ax < 3; ++ax) {

@@ -1010,6 +1010,29 @@ int fw_create_medium(const fw_grid *g, const float *c, const float *rho, const f
     return create_common(g, c, rho, beta, idx.data(), classes, storage, (cudaStream_t)stream, out);
 }
 
+// Source/receiver pairs on one cell: the combined injection-and-recording
+// kernel lets the source's thread record the receiver there (after the
+// injection), so no two threads touch one cell.  Both lists are sorted.
+static int upload_io_map(fw_medium *m, cudaStream_t s)
+{
+    const std::vector<long long> &a = m->h_src_idx, &b = m->h_rcv_idx;
+    std::vector<int> sr(a.size(), -1), rs(b.size(), -1);
+    for (size_t i = 0, j = 0; i < a.size() && j < b.size();) {
+        if (a[i] < b[j]) ++i;
+        else if (b[j] < a[i]) ++j;
+        else {
+            sr[i] = (int)j;
+            rs[j] = (int)i;
+            ++i;
+            ++j;
+        }
+    }
+    if (m->src_rcv && !sr.empty()) FW_CK(cudaMemcpyAsync(m->src_rcv, sr.data(), sr.size() * 4, cudaMemcpyHostToDevice, s));
+    if (m->rcv_src && !rs.empty()) FW_CK(cudaMemcpyAsync(m->rcv_src, rs.data(), rs.size() * 4, cudaMemcpyHostToDevice, s));
+    FW_CK(cudaStreamSynchronize(s));
+    return FW_OK;
+}
+
 int fw_set_sources(fw_medium *m, const uint8_t *mask, const float *waveforms, int n_wave, int n_steps,
                    const int32_t *wave_of_src)
 {
@@ -1031,17 +1054,21 @@ int fw_set_sources(fw_medium *m, const uint8_t *mask, const float *waveforms, in
     drop_graphs(m);
     dev_free(m->src_buf);
     m->src_buf = nullptr;
+    m->src_rcv = nullptr;
     m->n_src = 0;
-    if (ns == 0) return FW_OK;
+    m->h_src_idx.clear();
+    if (ns == 0) return upload_io_map(m, s);
     const size_t wl = (size_t)n_wave * n_steps;
     const size_t o_idx = 0, o_gain = align_up(ns * 8, 256), o_wof = o_gain + align_up((size_t)ns * m->es, 256),
-                 o_wave = o_wof + align_up((size_t)ns * 4, 256), total = o_wave + align_up(wl * m->es, 256);
+                 o_map = o_wof + align_up((size_t)ns * 4, 256), o_wave = o_map + align_up((size_t)ns * 4, 256),
+                 total = o_wave + align_up(wl * m->es, 256);
     m->src_buf = dev_alloc(total);
     if (!m->src_buf) return FW_ERR_NOMEM;
     char *b = static_cast<char *>(m->src_buf);
     m->src_idx = reinterpret_cast<long long *>(b + o_idx);
     m->src_gain = b + o_gain;
     m->wave_of = reinterpret_cast<int *>(b + o_wof);
+    m->src_rcv = reinterpret_cast<int *>(b + o_map);
     m->waves = b + o_wave;
     // every upload is ordered on the medium's stream and complete before
     // return: later work on any other (non-blocking) stream reads these
@@ -1063,6 +1090,8 @@ int fw_set_sources(fw_medium *m, const uint8_t *mask, const float *waveforms, in
     m->n_src = ns;
     m->n_wave = n_wave;
     m->wave_len = n_steps;
+    m->h_src_idx = std::move(idx);
+    if (int rc = upload_io_map(m, s)) return rc;
     if (m->storage == FW_STORE_F16) return set_psi_reference(m, waveforms, wl);
     return FW_OK;
 }
@@ -1076,16 +1105,20 @@ int fw_set_receivers(fw_medium *m, const uint8_t *mask, int decim, int n_steps)
     drop_graphs(m);
     dev_free(m->rcv_buf);
     m->rcv_buf = nullptr;
+    m->rcv_src = nullptr;
     m->n_rcv = 0;
     m->n_rec = 0;
+    m->h_rcv_idx.clear();
     const int nr = (int)idx.size();
-    if (nr == 0) return FW_OK;
+    if (nr == 0) return upload_io_map(m, s);
     const int nrec = (n_steps + decim - 1) / decim;
-    const size_t o_tr = align_up((size_t)nr * 8, 256), total = o_tr + align_up((size_t)nr * std::max(nrec, 1) * m->es, 256);
+    const size_t o_map = align_up((size_t)nr * 8, 256), o_tr = o_map + align_up((size_t)nr * 4, 256),
+                 total = o_tr + align_up((size_t)nr * std::max(nrec, 1) * m->es, 256);
     m->rcv_buf = dev_alloc(total);
     if (!m->rcv_buf) return FW_ERR_NOMEM;
     char *b = static_cast<char *>(m->rcv_buf);
     m->rcv_idx = reinterpret_cast<long long *>(b);
+    m->rcv_src = reinterpret_cast<int *>(b + o_map);
     m->traces = b + o_tr;
     // ordered on the medium's stream and complete before return (see fw_set_sources)
     FW_CK(cudaMemcpyAsync(m->rcv_idx, idx.data(), nr * 8, cudaMemcpyHostToDevice, s));
@@ -1094,7 +1127,8 @@ int fw_set_receivers(fw_medium *m, const uint8_t *mask, int decim, int n_steps)
     m->n_rcv = nr;
     m->n_rec = nrec;
     m->decim = decim;
-    return FW_OK;
+    m->h_rcv_idx = std::move(idx);
+    return upload_io_map(m, s);
 }
 
 int fw_step(fw_medium *m, int n_steps, void *stream)
@@ -1163,7 +1197,7 @@ int fw_step_timed(fw_medium *m, int n_steps, void *stream, double *ms_velocity, 
             cudaEventRecord(ev[3 * j + 1], s) != cudaSuccess || launch_sweep(m, s, 2) != cudaSuccess ||
             cudaEventRecord(ev[3 * j + 2], s) != cudaSuccess || launch_io_any(m, j, s) != cudaSuccess)
             rc = FW_ERR_CUDA;
-        launches += 2 + (m->n_src > 0) + (m->n_rcv > 0);
+        launches += 2 + (m->n_src + m->n_rcv > 0);
     }
     if (rc == FW_OK) {
         k_advance<<<1, 1, 0, s>>>(m->d_it, n_steps);

@@ -60,6 +60,15 @@ struct PresMaps {
     TensorMapBlob vx_ring, vy_ring, vz_ring;   // time-space stencil: v boxes with x and y halos
 };
 
+// A step between two state images (buffers laid out as the medium's state):
+// every state array is read at its offset in the image at rd and written at
+// the same offset in the image wofs bytes further on; maps and tables stay
+// the medium's.
+struct StepImages {
+    const char *rd;
+    long long wofs;
+};
+
 struct Graph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -97,6 +106,11 @@ struct fw_medium {
     int *wave_of = nullptr;
     int n_src = 0, n_wave = 0, wave_len = 0;
     int n_rcv = 0, n_rec = 0, decim = 1;
+    // cells that hold both a source and a receiver: per source the receiver
+    // there (or -1), per receiver the source there (or -1); host copies of
+    // both index lists to rebuild them
+    int *src_rcv = nullptr, *rcv_src = nullptr;
+    std::vector<long long> h_src_idx, h_rcv_idx;
     // bookkeeping
     long long step = 0;
     int sticky = 0;

@@ -324,6 +324,8 @@ template <typename R, typename SS, typename SP> struct VelArgs {
     const R *pd[3], *pa[3];      // absorbing profile at half points per axis
     const SS *kdt;               // K dt per voxel (time-space stencil only)
     Monitor *mon;                // failure record (a staged-copy wait that gave up)
+    long long wofs;              // bytes from each state array read to where it is written
+                                 // (0: in place; per-thread staging only)
     VelMaps maps;                // tensor maps of the staged streams (TMA staging only)
 };
 
@@ -340,8 +342,17 @@ template <typename R, typename SS, typename SP> struct PresArgs {
     const R *pd[3], *pa[3];      // absorbing profile at integer points per axis
     Monitor *mon;
     const SS *rho;               // density per voxel (time-space stencil only)
+    long long wofs;              // as VelArgs::wofs
     PresMaps maps;               // tensor maps of the staged streams (TMA staging only)
 };
+
+// Where a sweep stores a state array it read at p: wofs bytes further on for
+// a step from one state image into another (the adjoint's recomputation),
+// p itself for the in-place step.
+template <typename T> __device__ __forceinline__ T *wr_at(T *p, long long wofs)
+{
+    return reinterpret_cast<T *>(reinterpret_cast<char *>(p) + wofs);
+}
 
 template <typename SS, typename R>
 __device__ __forceinline__ void ld4_or_zero(const SS *base, bool ok, R (&v)[4])
@@ -865,10 +876,10 @@ k_velocity(const __grid_constant__ VelArgs<R, SS, SP> A)
                     }
                     vv[e] = live ? vv[e] - dtr[ax][e] * stv : R(0);
                 }
-                Io<SS>::st(A.v[ax] + pk + row, vv);
+                Io<SS>::st(wr_at(A.v[ax] + pk + row, TMA ? 0LL : A.wofs), vv);
 #pragma unroll
-                for (int m = 0; m < NM; ++m) Io<SP>::st(A.psi[m][ax] + pk + row, ps[m]);
-                if (pml_here) Io<SS>::st(A.psip[ax] + pk + row, pp);
+                for (int m = 0; m < NM; ++m) Io<SP>::st(wr_at(A.psi[m][ax] + pk + row, TMA ? 0LL : A.wofs), ps[m]);
+                if (pml_here) Io<SS>::st(wr_at(A.psip[ax] + pk + row, TMA ? 0LL : A.wofs), pp);
             }
         }
 #pragma unroll
@@ -1432,13 +1443,13 @@ k_pressure(const __grid_constant__ PresArgs<R, SS, SP> A)
                 bad |= !(ap <= R(3.0e38));
                 pmax = fmax(pmax, ap);
             }
-            Io<SS>::st(A.p + pk + row, pv);
+            Io<SS>::st(wr_at(A.p + pk + row, TMA ? 0LL : A.wofs), pv);
 #pragma unroll
-            for (int m = 0; m < NM; ++m) Io<SP>::st(A.psi[m] + pk + row, ps[m]);
+            for (int m = 0; m < NM; ++m) Io<SP>::st(wr_at(A.psi[m] + pk + row, TMA ? 0LL : A.wofs), ps[m]);
 #pragma unroll
             for (int ax = 0; ax < 3; ++ax) {
                 const bool pml_here = ax == 0 ? pml_x : (ax == 1 ? pml_y : pml_z);
-                if (pml_here) Io<SS>::st(A.psip[ax] + pk + row, pp[ax]);
+                if (pml_here) Io<SS>::st(wr_at(A.psip[ax] + pk + row, TMA ? 0LL : A.wofs), pp[ax]);
             }
         }
 #pragma unroll
@@ -1484,22 +1495,45 @@ __global__ void k_sources(SS *p, const long long *idx, const R *gain, const int 
     }
 }
 
-template <typename SS>
-__global__ void k_receivers(const SS *p, const long long *idx, SS *traces, int n_rcv, int n_rec,
-                            int decim, const int *d_it, int j, long long vol, Monitor *mon)
+// Injection and recording of step it = *d_it + j in one launch: threads
+// [0, n_src) inject the sources (and record the receiver on a source's cell,
+// src_rcv, after the injection); threads [n_src, n_src + n_rcv) record the
+// other receivers.  No two threads touch one cell.
+template <typename SS, typename R>
+__global__ void k_io(SS *p, const long long *src_idx, const R *gain, const int *wave_of, const R *waves,
+                     int wave_len, int n_src, const int *src_rcv, const long long *rcv_idx, const int *rcv_src,
+                     SS *traces, int n_rcv, int n_rec, int decim, const int *d_it, int j, long long vol,
+                     Monitor *mon)
 {
     const int it = *d_it + j;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (it < 0) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&mon->bad_index, 1);
+        if (t == 0) atomicExch(&mon->bad_index, 1);
         return;
     }
-    if (it % decim != 0 || it / decim >= n_rec) return;
-    const int col = it / decim;
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n_rcv; r += gridDim.x * blockDim.x) {
-        const long long k = idx[r];
+    const bool rec = n_rcv > 0 && it % decim == 0 && it / decim < n_rec;
+    const size_t col = rec ? (size_t)(it / decim) : 0;
+    if (t < n_src) {
+        const long long k = src_idx[t];
+        if (k < 0 || k >= vol) {     // never for a consistent medium: record, skip
+            atomicExch(&mon->bad_index, 1);
+            return;
+        }
+        const int r = rec ? src_rcv[t] : -1;
+        if (it < wave_len) {
+            const SS v = SS(R(p[k]) + gain[t] * waves[(size_t)wave_of[t] * wave_len + it]);
+            p[k] = v;
+            if (r >= 0) traces[(size_t)r * n_rec + col] = v;
+        } else if (r >= 0) {
+            traces[(size_t)r * n_rec + col] = p[k];
+        }
+    } else if (rec && t < n_src + n_rcv) {
+        const int r = t - n_src;
+        if (rcv_src[r] >= 0) return;     // recorded by the thread of the source on its cell
+        const long long k = rcv_idx[r];
         if (k < 0 || k >= vol) {
             atomicExch(&mon->bad_index, 1);
-            continue;
+            return;
         }
         traces[(size_t)r * n_rec + col] = p[k];
     }

@@ -114,9 +114,11 @@ bool build_vel_maps_t(EncodeTiledFn encode, fw_medium *m)
 
 // which: bit 0 = velocity sweep, bit 1 = pressure sweep, bit 2 = only opt the
 // instances into their dynamic shared memory (done once at medium creation,
-// outside any stream capture)
+// outside any stream capture).  im (may be null): a step from one state
+// image into another (StepImages) instead of the in-place step of the
+// medium's own state.
 template <typename R, typename SS, typename SP, int DIM, int NM, bool TS>
-cudaError_t launch_dn(const fw_medium *m, cudaStream_t s, int which)
+cudaError_t launch_dn(const fw_medium *m, cudaStream_t s, int which, const StepImages *im)
 {
     constexpr int BX = DIM == 3 ? Tile3<R>::BX : Tile2<R>::BX;
     constexpr int BYV = DIM == 3 ? Tile3<R>::BYV : Tile2<R>::BYV;
@@ -153,16 +155,26 @@ cudaError_t launch_dn(const fw_medium *m, cudaStream_t s, int which)
     }
     const Geo<R> g = make_geo<R>(m);
     const int gx = (m->NX + 4 * BX - 1) / (4 * BX), gz = (m->NZ + m->zseg - 1) / m->zseg;
+    // a state array of the medium, or the same array in the image read (rd)
+    // or written (nw) by an image step
+    const char *slab = static_cast<const char *>(m->slab);
+    auto rd = [&](void *a) -> void * {
+        return (a && im) ? const_cast<char *>(im->rd) + (static_cast<const char *>(a) - slab) : a;
+    };
+    auto nw = [&](void *a) -> void * { return (a && im) ? static_cast<char *>(rd(a)) + im->wofs : a; };
+    const long long wofs = im ? im->wofs : 0;
+    const bool tma = m->tma && !im;   // tensor maps address the medium's own arrays
 
     VelArgs<R, SS, SP> va{};
     va.g = g;
-    va.p = static_cast<const SS *>(m->p);
+    va.p = static_cast<const SS *>(rd(m->p));
+    va.wofs = wofs;
     for (int ax = 0; ax < 3; ++ax) {
-        va.v[ax] = static_cast<SS *>(m->v[ax]);
-        va.psip[ax] = static_cast<SS *>(m->psi1p[ax]);
+        va.v[ax] = static_cast<SS *>(rd(m->v[ax]));
+        va.psip[ax] = static_cast<SS *>(rd(m->psi1p[ax]));
         va.pd[ax] = static_cast<const R *>(m->prof[ax][0]);
         va.pa[ax] = static_cast<const R *>(m->prof[ax][1]);
-        for (int n = 0; n < NM; ++n) va.psi[n][ax] = static_cast<SP *>(m->psi1[n][ax]);
+        for (int n = 0; n < NM; ++n) va.psi[n][ax] = static_cast<SP *>(rd(m->psi1[n][ax]));
     }
     va.rho = static_cast<const SS *>(m->rho);
     va.cls = m->cls;
@@ -173,7 +185,7 @@ cudaError_t launch_dn(const fw_medium *m, cudaStream_t s, int which)
         const dim3 gv(gx, (m->NY + BYV - 1) / BYV, gz), bv(BX, BYV);
         bool done = false;
         if constexpr (CAN_TMA) {
-            if (m->tma) {
+            if (tma) {
                 va.maps = m->vel_maps;
                 k_velocity<R, SS, SP, DIM, NM, BX, BYV, TS, true><<<gv, bv, LVT::bytes, s>>>(va);
                 done = true;
@@ -185,14 +197,15 @@ cudaError_t launch_dn(const fw_medium *m, cudaStream_t s, int which)
 
     PresArgs<R, SS, SP> pa{};
     pa.g = g;
-    pa.p = static_cast<SS *>(m->p);
+    pa.p = static_cast<SS *>(rd(m->p));
+    pa.wofs = wofs;
     for (int ax = 0; ax < 3; ++ax) {
-        pa.v[ax] = static_cast<const SS *>(m->v[ax]);
-        pa.psip[ax] = static_cast<SS *>(m->psi2p[ax]);
+        pa.v[ax] = static_cast<const SS *>(nw(m->v[ax]));   // this step's velocity
+        pa.psip[ax] = static_cast<SS *>(rd(m->psi2p[ax]));
         pa.pd[ax] = static_cast<const R *>(m->prof[ax][2]);
         pa.pa[ax] = static_cast<const R *>(m->prof[ax][3]);
     }
-    for (int n = 0; n < NM; ++n) pa.psi[n] = static_cast<SP *>(m->psi2[n]);
+    for (int n = 0; n < NM; ++n) pa.psi[n] = static_cast<SP *>(rd(m->psi2[n]));
     pa.kdt = static_cast<const SS *>(m->kdt);
     pa.b2dt = static_cast<const SS *>(m->b2dt);
     pa.cls = m->cls;
@@ -201,7 +214,7 @@ cudaError_t launch_dn(const fw_medium *m, cudaStream_t s, int which)
     pa.rho = static_cast<const SS *>(m->rho);
     const dim3 gp(gx, (m->NY + BYP - 1) / BYP, gz), bp(BX, BYP);
     if constexpr (CAN_TMA) {
-        if (m->tma) {
+        if (tma) {
             pa.maps = m->pres_maps;
             if (m->nonlinear)
                 k_pressure<R, SS, SP, DIM, NM, BX, BYP, true, TS, true><<<gp, bp, LPT::bytes, s>>>(pa);
@@ -218,41 +231,55 @@ cudaError_t launch_dn(const fw_medium *m, cudaStream_t s, int which)
 }
 
 template <typename R, typename SS, typename SP, bool TS>
-cudaError_t launch_ts(const fw_medium *m, cudaStream_t s, int which)
+cudaError_t launch_ts(const fw_medium *m, cudaStream_t s, int which, const StepImages *im)
 {
     const bool d3 = m->ndim == 3;
     switch (m->nmech) {
-    case 1: return d3 ? launch_dn<R, SS, SP, 3, 1, TS>(m, s, which) : launch_dn<R, SS, SP, 2, 1, TS>(m, s, which);
-    case 2: return d3 ? launch_dn<R, SS, SP, 3, 2, TS>(m, s, which) : launch_dn<R, SS, SP, 2, 2, TS>(m, s, which);
-    case 3: return d3 ? launch_dn<R, SS, SP, 3, 3, TS>(m, s, which) : launch_dn<R, SS, SP, 2, 3, TS>(m, s, which);
-    case 4: return d3 ? launch_dn<R, SS, SP, 3, 4, TS>(m, s, which) : launch_dn<R, SS, SP, 2, 4, TS>(m, s, which);
+    case 1: return d3 ? launch_dn<R, SS, SP, 3, 1, TS>(m, s, which, im) : launch_dn<R, SS, SP, 2, 1, TS>(m, s, which, im);
+    case 2: return d3 ? launch_dn<R, SS, SP, 3, 2, TS>(m, s, which, im) : launch_dn<R, SS, SP, 2, 2, TS>(m, s, which, im);
+    case 3: return d3 ? launch_dn<R, SS, SP, 3, 3, TS>(m, s, which, im) : launch_dn<R, SS, SP, 2, 3, TS>(m, s, which, im);
+    case 4: return d3 ? launch_dn<R, SS, SP, 3, 4, TS>(m, s, which, im) : launch_dn<R, SS, SP, 2, 4, TS>(m, s, which, im);
     default: return cudaErrorInvalidValue;
     }
 }
 
 // leapfrog instances, or those of the time-space stencil (time_order 4)
 template <typename R, typename SS, typename SP>
-cudaError_t launch_sweeps(const fw_medium *m, cudaStream_t s, int which)
+cudaError_t launch_sweeps(const fw_medium *m, cudaStream_t s, int which, const StepImages *im = nullptr)
 {
-    return m->time_order == 4 ? launch_ts<R, SS, SP, true>(m, s, which) : launch_ts<R, SS, SP, false>(m, s, which);
+    return m->time_order == 4 ? launch_ts<R, SS, SP, true>(m, s, which, im)
+                              : launch_ts<R, SS, SP, false>(m, s, which, im);
+}
+
+// One leapfrog step from the state image at im.rd into the one at
+// im.rd + im.wofs (both laid out as the medium's state), sources included at
+// step it (absolute); receivers are not recorded and the images' step
+// counters are not used.  For the adjoint's recomputation: no copy of the
+// state per step, the medium's own state untouched.
+template <typename R, typename SS>
+cudaError_t launch_image_step(const fw_medium *m, const StepImages &im, const int *zero, int it, cudaStream_t s)
+{
+    cudaError_t e = launch_sweeps<R, SS, SS>(m, s, 3, &im);
+    if (e != cudaSuccess || m->n_src <= 0) return e;
+    SS *p = reinterpret_cast<SS *>(const_cast<char *>(im.rd) + im.wofs +
+                                   (static_cast<const char *>(m->p) - static_cast<const char *>(m->slab)));
+    k_sources<SS, R><<<(m->n_src + 255) / 256, 256, 0, s>>>(p, m->src_idx, static_cast<const R *>(m->src_gain),
+                                                           m->wave_of, static_cast<const R *>(m->waves),
+                                                           m->wave_len, m->n_src, zero, it, (long long)m->vol,
+                                                           m->mon);
+    return cudaGetLastError();
 }
 
 template <typename R, typename SS>
 cudaError_t launch_io(const fw_medium *m, int j, cudaStream_t s)
 {
-    if (m->n_src > 0) {
-        int nb = (m->n_src + 255) / 256;
-        k_sources<SS, R><<<nb, 256, 0, s>>>(static_cast<SS *>(m->p), m->src_idx,
-                                            static_cast<const R *>(m->src_gain), m->wave_of,
-                                            static_cast<const R *>(m->waves), m->wave_len, m->n_src,
-                                            m->d_it, j, (long long)m->vol, m->mon);
-    }
-    if (m->n_rcv > 0) {
-        int nb = (m->n_rcv + 255) / 256;
-        k_receivers<SS><<<nb, 256, 0, s>>>(static_cast<const SS *>(m->p), m->rcv_idx,
-                                           static_cast<SS *>(m->traces), m->n_rcv, m->n_rec,
-                                           m->decim, m->d_it, j, (long long)m->vol, m->mon);
-    }
+    const int n = m->n_src + m->n_rcv;
+    if (n <= 0) return cudaSuccess;
+    k_io<SS, R><<<(n + 255) / 256, 256, 0, s>>>(static_cast<SS *>(m->p), m->src_idx,
+                                                 static_cast<const R *>(m->src_gain), m->wave_of,
+                                                 static_cast<const R *>(m->waves), m->wave_len, m->n_src, m->src_rcv,
+                                                 m->rcv_idx, m->rcv_src, static_cast<SS *>(m->traces), m->n_rcv,
+                                                 m->n_rec, m->decim, m->d_it, j, (long long)m->vol, m->mon);
     return cudaGetLastError();
 }
 

@@ -96,6 +96,27 @@ def test_gradient_matches_oracle(fw, shape):
         assert rel_l2(tr, orc["traces"]) < (2e-10 if storage == "f64" else 1e-5)
 
 
+@pytest.mark.parametrize("shape", [(60, 52), (18, 16, 20)])
+def test_gradient_receiver_on_the_source_cell(fw, shape):
+    """A receiver on the source cell and one beside it: the transpose of the
+    combined injection and recording adds that receiver's adjoint before the
+    source-gain term reads the pressure adjoint there."""
+    n_steps = 140 if len(shape) == 2 else 80
+    P = _problem(shape, seed=11, n_steps=n_steps, pml=6 if len(shape) == 2 else 3)
+    at_src = tuple(int(i[0]) for i in np.nonzero(P["src"]))
+    beside = (at_src[0] + 1,) + at_src[1:]
+    P["rcv"][at_src] = 1
+    P["rcv"][beside] = 1
+    P["G"] = np.random.default_rng(12).standard_normal((int(P["rcv"].sum()), n_steps))
+    orc = _oracle_grad(P)
+    for storage, tol in (("f64", 1e-12), ("f32", 1e-4)):
+        gc, ga, tr, _ = _gpu_grad(fw, P, storage)
+        ec, ea = rel_l2(gc, orc["grad_c"]), rel_l2(ga, orc["grad_alpha0"])
+        print("\n%s %s: grad_c rel L2 %.2e, grad_alpha0 rel L2 %.2e" % (shape, storage, ec, ea))
+        assert ec < tol and ea < tol, (storage, ec, ea)
+        assert rel_l2(tr, orc["traces"]) < (2e-10 if storage == "f64" else 1e-5)
+
+
 def test_gradient_checkpoint_interval_does_not_matter(fw):
     P = _problem((40, 36), seed=7, n_steps=120)
     ref = _gpu_grad(fw, P, "f64", checkpoint=120)

@@ -66,6 +66,32 @@ def test_c2_two_layer_nonlinear_crop(fw, storage):
     _check(pr.run_compare(500, f64=storage == "f64"), TOL[storage])
 
 
+@pytest.mark.parametrize("shape", [(80, 72), (24, 30, 28)])
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_receivers_on_source_cells(fw, shape, storage):
+    """Injection and recording share one launch: receivers on some source
+    cells record p after the injection (as the oracle does), receivers beside
+    them record as usual, every second step (decimation 2), and the waveform
+    ends before the run does (the last 60 steps record without injection)."""
+    f0 = 3e6
+    dx = 1540.0 / (f0 * 12)
+    one = np.ones(shape, np.float32)
+    dt = 0.3 * dx / 1540.0
+    n_steps = 200
+    src = np.zeros(shape, np.uint8)
+    src[(8,) + tuple(slice(4, n - 4) for n in shape[1:])] = 1
+    rcv = np.zeros(shape, np.uint8)
+    rcv[(8,) + tuple(slice(2, n - 2, 3) for n in shape[1:])] = 1      # on and beside the source cells
+    rcv[(shape[0] - 9,) + tuple(slice(2, n - 2, 5) for n in shape[1:])] = 1
+    assert (src & rcv).sum() > 1 and (rcv & ~src).sum() > 1
+    waves = gaussian_pulse(f0, dt, n_steps - 60, 1e-3 if len(shape) == 2 else 1e-6)[None].astype(np.float32)
+    pr = Pair(fw, shape, dx, dt, 1540 * one, 1000 * one, np.zeros(shape, np.uint16), [oracle_params(0.5, 1.1, 2)],
+              pml=6, f0=f0, storage=storage)
+    pr.sources(src, waves)
+    pr.receivers(rcv, n_steps, decim=2)
+    _check(pr.run_compare(n_steps, f64=storage == "f64"), TOL[storage])
+
+
 @pytest.mark.parametrize("storage", ["f64", "f32"])
 def test_c3_voronoi_3d_crop(fw, storage):
     """96^3 crop of the 512^3 Voronoi map (8 classes, N=4, jittered c/rho),
