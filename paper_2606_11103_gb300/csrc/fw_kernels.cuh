@@ -373,16 +373,18 @@ __device__ __forceinline__ void ld4_or_zero(const SS *base, bool ok, R (&v)[4])
 template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY, bool TS = false, bool TMA = false>
 struct VelSmem {
     static constexpr int TW = 4 * BX, SW = TW + 8, SH = DIM == 3 ? BY + 7 : BY, RO = DIM == 3 ? 3 : 0;
+    // per-axis tiles: one slot per axis of the grid (2D: x in slot 0, depth in slot 1)
     static constexpr int NAX = DIM == 3 ? 3 : 2;
+    static __host__ __device__ constexpr int slot(int ax) { return DIM == 3 ? ax : (ax == 2 ? 1 : ax); }
     static constexpr size_t TILE = (size_t)BY * TW;
     // per stage (bytes, 16-aligned pieces)
     static constexpr size_t o_v = 0;
-    static constexpr size_t o_psi = o_v + 3 * TILE * sizeof(SS);
-    static constexpr size_t o_pn = o_psi + (size_t)NM * 3 * TILE * sizeof(SP);
+    static constexpr size_t o_psi = o_v + NAX * TILE * sizeof(SS);
+    static constexpr size_t o_pn = o_psi + (size_t)NM * NAX * TILE * sizeof(SP);
     static constexpr size_t o_rn = o_pn + TILE * sizeof(SS);
     static constexpr size_t o_cls = o_rn + TILE * sizeof(SS);
     static constexpr size_t o_pml = o_cls + (TILE * 2 + 15) / 16 * 16;     // absorbing-layer psi per axis
-    static constexpr size_t o_kv = o_pml + 3 * TILE * sizeof(SS);          // K dt of plane k (time-space only)
+    static constexpr size_t o_kv = o_pml + NAX * TILE * sizeof(SS);        // K dt of plane k (time-space only)
     static constexpr size_t stage = (o_kv + (TS ? TILE * sizeof(SS) : 0) + 127) / 128 * 128;
     // derivative tiles of p (x/y halos) and rho (+1 halos), two each; every
     // buffer starts on 128 bytes (TMA destinations)
@@ -399,12 +401,14 @@ struct VelSmem {
     // bytes the TMA copies of one plane deliver (completion count of its barrier)
     static constexpr unsigned tma_bytes =
         (unsigned)(((size_t)SH * SW + (size_t)(BY + 1) * (TW + 4)) * sizeof(SS) +
-                   TILE * (5 + (TS ? 1 : 0)) * sizeof(SS) + (size_t)NM * 3 * TILE * sizeof(SP) + TILE * 2);
+                   TILE * (5 + (TS ? 1 : 0)) * sizeof(SS) + (size_t)NM * NAX * TILE * sizeof(SP) + TILE * 2);
 };
 
 template <typename R, typename SS, typename SP, int DIM, int NM, int BX, int BY, bool TS = false, bool TMA = false>
 struct PresSmem {
     static constexpr int TW = 4 * BX, SWX = TW + 8, SHY = DIM == 3 ? BY + 7 : 1;
+    static constexpr int NAX = DIM == 3 ? 3 : 2;   // absorbing-layer tiles: one slot per axis of the grid
+    static __host__ __device__ constexpr int slot(int ax) { return DIM == 3 ? ax : (ax == 2 ? 1 : ax); }
     static constexpr size_t TILE = (size_t)BY * TW;
     static constexpr size_t o_qn = 0;
     static constexpr size_t o_p = o_qn + TILE * sizeof(SS);
@@ -413,7 +417,7 @@ struct PresSmem {
     static constexpr size_t o_psi = o_bd + TILE * sizeof(SS);
     static constexpr size_t o_cls = o_psi + (size_t)NM * TILE * sizeof(SP);
     static constexpr size_t o_pml = o_cls + (TILE * 2 + 15) / 16 * 16;
-    static constexpr size_t o_rh = o_pml + 3 * TILE * sizeof(SS);          // rho of plane k (time-space only)
+    static constexpr size_t o_rh = o_pml + NAX * TILE * sizeof(SS);        // rho of plane k (time-space only)
     static constexpr size_t stage = (o_rh + (TS ? TILE * sizeof(SS) : 0) + 127) / 128 * 128;
     // v_x (x halo) and v_y (y halo) tiles, two each, on 128-byte boundaries
     // (the time-space stencil with TMA staging uses the rings below instead)
@@ -453,10 +457,10 @@ __device__ __forceinline__ void vel_issue_tma(const VelArgs<R, SS, SP> &A, unsig
     mbar_expect_tx(bar, L::tma_bytes);
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
-        tma_load_3d(st + L::o_v + ax * L::TILE * sizeof(SS), &A.maps.v[ax], xb, yb, k, bar);
+        tma_load_3d(st + L::o_v + L::slot(ax) * L::TILE * sizeof(SS), &A.maps.v[ax], xb, yb, k, bar);
 #pragma unroll
         for (int m = 0; m < NM; ++m)
-            tma_load_3d(st + L::o_psi + (m * 3 + ax) * L::TILE * sizeof(SP), &A.maps.psi[m][ax], xb, yb, k, bar);
+            tma_load_3d(st + L::o_psi + (m * L::NAX + L::slot(ax)) * L::TILE * sizeof(SP), &A.maps.psi[m][ax], xb, yb, k, bar);
     }
     tma_load_3d(st + L::o_pn, &A.maps.p_own, xb, yb, k + 4, bar);
     tma_load_3d(st + L::o_rn, &A.maps.rho_own, xb, yb, k + 1, bar);
@@ -484,7 +488,7 @@ __device__ __forceinline__ void vel_issue(const VelArgs<R, SS, SP> &A, unsigned 
                                 k < G.wabs || k >= G.nz - G.wabs};
 #pragma unroll
             for (int ax = 0; ax < 3; ++ax)
-                if (in[ax]) cp_async4(reinterpret_cast<SS *>(st + L::o_pml) + ax * L::TILE + e0, A.psip[ax] + pk + row, true);
+                if (in[ax]) cp_async4(reinterpret_cast<SS *>(st + L::o_pml) + L::slot(ax) * L::TILE + e0, A.psip[ax] + pk + row, true);
         }
         return;
     }
@@ -492,10 +496,10 @@ __device__ __forceinline__ void vel_issue(const VelArgs<R, SS, SP> &A, unsigned 
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
         if (DIM == 2 && ax == 1) continue;
-        cp_async4(reinterpret_cast<SS *>(st + L::o_v) + ax * L::TILE + e0, hd ? A.v[ax] + pk + row : gz, hd);
+        cp_async4(reinterpret_cast<SS *>(st + L::o_v) + L::slot(ax) * L::TILE + e0, hd ? A.v[ax] + pk + row : gz, hd);
 #pragma unroll
         for (int m = 0; m < NM; ++m)
-            cp_async4(reinterpret_cast<SP *>(st + L::o_psi) + (m * 3 + ax) * L::TILE + e0,
+            cp_async4(reinterpret_cast<SP *>(st + L::o_psi) + (m * L::NAX + L::slot(ax)) * L::TILE + e0,
                       hd ? A.psi[m][ax] + pk + row : reinterpret_cast<const SP *>(gz), hd);
     }
     {
@@ -511,7 +515,7 @@ __device__ __forceinline__ void vel_issue(const VelArgs<R, SS, SP> &A, unsigned 
                             k < G.wabs || k >= G.nz - G.wabs};
 #pragma unroll
         for (int ax = 0; ax < 3; ++ax)
-            if (in[ax]) cp_async4(reinterpret_cast<SS *>(st + L::o_pml) + ax * L::TILE + e0, A.psip[ax] + pk + row, true);
+            if (in[ax]) cp_async4(reinterpret_cast<SS *>(st + L::o_pml) + L::slot(ax) * L::TILE + e0, A.psip[ax] + pk + row, true);
     }
     // halos of plane k straight into the derivative tiles of parity k&1
     R *sp = reinterpret_cast<R *>(sm + L::o_sp + (k & 1) * L::sp_stride);
@@ -831,13 +835,13 @@ k_velocity(const __grid_constant__ VelArgs<R, SS, SP> A)
             for (int ax = 0; ax < 3; ++ax) {
                 if (DIM == 2 && ax == 1) continue;
                 R vv[4], ps[NM][4];
-                Sm<SS>::ld(reinterpret_cast<const SS *>(st + L::o_v) + ax * L::TILE + e0, vv);
+                Sm<SS>::ld(reinterpret_cast<const SS *>(st + L::o_v) + L::slot(ax) * L::TILE + e0, vv);
 #pragma unroll
                 for (int m = 0; m < NM; ++m)
-                    Sm<SP>::ld(reinterpret_cast<const SP *>(st + L::o_psi) + (m * 3 + ax) * L::TILE + e0, ps[m]);
+                    Sm<SP>::ld(reinterpret_cast<const SP *>(st + L::o_psi) + (m * L::NAX + L::slot(ax)) * L::TILE + e0, ps[m]);
                 const bool pml_here = ax == 0 ? pml_x : (ax == 1 ? pml_y : pml_z);
                 R pp[4];
-                if (pml_here) Sm<SS>::ld(reinterpret_cast<const SS *>(st + L::o_pml) + ax * L::TILE + e0, pp);
+                if (pml_here) Sm<SS>::ld(reinterpret_cast<const SS *>(st + L::o_pml) + L::slot(ax) * L::TILE + e0, pp);
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     const int c = cls4[e];
@@ -1086,7 +1090,7 @@ __device__ __forceinline__ void pres_issue(const PresArgs<R, SS, SP> &A, unsigne
                                 k < G.wabs || k >= G.nz - G.wabs};
 #pragma unroll
             for (int ax = 0; ax < 3; ++ax)
-                if (in[ax]) cp_async4(reinterpret_cast<SS *>(st + L::o_pml) + ax * L::TILE + e0, A.psip[ax] + pk + row, true);
+                if (in[ax]) cp_async4(reinterpret_cast<SS *>(st + L::o_pml) + L::slot(ax) * L::TILE + e0, A.psip[ax] + pk + row, true);
         }
         return;
     }
@@ -1109,7 +1113,7 @@ __device__ __forceinline__ void pres_issue(const PresArgs<R, SS, SP> &A, unsigne
                             k < G.wabs || k >= G.nz - G.wabs};
 #pragma unroll
         for (int ax = 0; ax < 3; ++ax)
-            if (in[ax]) cp_async4(reinterpret_cast<SS *>(st + L::o_pml) + ax * L::TILE + e0, A.psip[ax] + pk + row, true);
+            if (in[ax]) cp_async4(reinterpret_cast<SS *>(st + L::o_pml) + L::slot(ax) * L::TILE + e0, A.psip[ax] + pk + row, true);
     }
     // v_x (with x halo) and v_y (with y halo) of plane k straight into the tiles
     R *svx = reinterpret_cast<R *>(sm + L::o_svx + (k & 1) * L::svx_stride);
@@ -1378,7 +1382,7 @@ k_pressure(const __grid_constant__ PresArgs<R, SS, SP> A)
 #pragma unroll
             for (int ax = 0; ax < 3; ++ax) {
                 const bool pml_here = ax == 0 ? pml_x : (ax == 1 ? pml_y : pml_z);
-                if (pml_here) Sm<SS>::ld(reinterpret_cast<const SS *>(st + L::o_pml) + ax * L::TILE + e0, pp[ax]);
+                if (pml_here) Sm<SS>::ld(reinterpret_cast<const SS *>(st + L::o_pml) + L::slot(ax) * L::TILE + e0, pp[ax]);
             }
             R rr[4] = {R(1), R(1), R(1), R(1)};
             if (pml_x || pml_y || pml_z) {
