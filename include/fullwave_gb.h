@@ -367,9 +367,12 @@ int fw_load_state(fw_medium *m, const void *src, void *stream);
  * alpha0: the medium's alpha0 map [nx*ny*nz] (host or device), or NULL: then
  * grad_alpha0 receives dL/ds.  G, alpha0, grad_c, grad_alpha0 are float
  * (as_f64 = 0) or double (as_f64 = 1), C order, host or device; grad_c or
- * grad_alpha0 may be NULL.  Device memory: (ceil(n_steps/K) + K + 3) state
- * images (fw_state_bytes) plus 6 fields and 4 FP64 maps, from the installed
- * allocator, released before return.  Blocking.
+ * grad_alpha0 may be NULL.  Device memory: ceil(n_steps/K) + 2(K - 1) + 3
+ * state images (about fw_state_bytes each; 2D), or ceil(n_steps/K) +
+ * 2(K - 1) + 2 state images and 6 fields (3D), plus 4 FP64 maps and the two
+ * output maps, from the installed allocator, released before return.  The
+ * recomputation of one segment runs on a stream of its own beside the
+ * adjoint of the next.  Blocking.
  * Errors: FW_ERR_ARG, FW_ERR_UNSUPPORTED (nonlinear media, 16-bit storage, the
  * time-space stencil (time_order 4), more than 65535 points along either of
  * the two slower axes),
