@@ -102,19 +102,69 @@ cd model_k(const fw_relax_params &p, double om, double c)
     return (om / c) / std::sqrt(s);
 }
 
+// model_k in real arithmetic, for the objective's inner loop (the same
+// quantities, without the library's guarded complex division and square
+// root, whose care is not needed here: every pole has a > 0 and om > 0):
+//   gamma_i = sum_m e_m / (a_m + i om) = sum_m e_m (a_m - i om) / (a_m^2 + om^2),
+//   e_m = d_m / kappa_i^2, a_m = d_m / kappa_i + alpha_m;
+//   s = 1/(kappa1 kappa2) - gamma1/kappa2 - gamma2/kappa1 + gamma1 gamma2;
+//   k = (om/c) / sqrt(s) = (om/c) conj(sqrt(s)) / |s|, principal square root.
+struct PoleSet {
+    int n;
+    double e1[FW_MAX_MECH], a1[FW_MAX_MECH], e2[FW_MAX_MECH], a2[FW_MAX_MECH];
+    double k1, k2, inv_k1k2;
+    explicit PoleSet(const fw_relax_params &p) : n(p.n_mech), k1(p.kappa1), k2(p.kappa2)
+    {
+        inv_k1k2 = 1.0 / (p.kappa1 * p.kappa2);
+        for (int m = 0; m < n; ++m) {
+            e1[m] = p.d1[m] / (p.kappa1 * p.kappa1);
+            a1[m] = p.d1[m] / p.kappa1 + p.alpha1[m];
+            e2[m] = p.d2[m] / (p.kappa2 * p.kappa2);
+            a2[m] = p.d2[m] / p.kappa2 + p.alpha2[m];
+        }
+    }
+    void k(double om, double c, double &kr, double &ki) const
+    {
+        double g1r = 0, g1i = 0, g2r = 0, g2i = 0;
+        const double om2 = om * om;
+        for (int m = 0; m < n; ++m) {
+            const double q1 = e1[m] / (a1[m] * a1[m] + om2), q2 = e2[m] / (a2[m] * a2[m] + om2);
+            g1r += q1 * a1[m];
+            g1i -= q1 * om;
+            g2r += q2 * a2[m];
+            g2i -= q2 * om;
+        }
+        const double sr = inv_k1k2 - g1r / k2 - g2r / k1 + (g1r * g2r - g1i * g2i);
+        const double si = -g1i / k2 - g2i / k1 + (g1r * g2i + g1i * g2r);
+        const double r = std::sqrt(sr * sr + si * si);
+        double qr, qi;                                   // sqrt(s), real part >= 0
+        if (sr >= 0.0) {
+            qr = std::sqrt(0.5 * (r + sr));
+            qi = si / (2.0 * qr);
+        } else {
+            qi = std::copysign(std::sqrt(0.5 * (r - sr)), si);
+            qr = si / (2.0 * qi);
+        }
+        const double f = om / (c * r);
+        kr = f * qr;
+        ki = -f * qi;
+    }
+};
+
 struct Objective {
     const Band *b;
     double w, c0;
     int n_mech;
     double operator()(const double *th) const
     {
-        fw_relax_params p = params_from_theta(th, n_mech);
+        const PoleSet ps(params_from_theta(th, n_mech));
         const size_t n = b->k.size();
         double acc = 0.0;
         for (size_t j = 0; j < n; ++j) {
-            cd kp = model_k(p, b->om[j], c0);
-            double dr = (1.0 - w) * (b->k[j].real() - kp.real()) / b->range_re;
-            double di = w * (b->k[j].imag() - kp.imag()) / b->range_im;
+            double kr, ki;
+            ps.k(b->om[j], c0, kr, ki);
+            double dr = (1.0 - w) * (b->k[j].real() - kr) / b->range_re;
+            double di = w * (b->k[j].imag() - ki) / b->range_im;
             acc += dr * dr + di * di;
         }
         return acc / double(n);
