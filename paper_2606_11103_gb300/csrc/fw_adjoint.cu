@@ -990,6 +990,8 @@ int gradient_impl(fw_medium *m, int n_steps, int K, const void *G, const void *a
     char *segs[2] = {static_cast<char *>(seg0.p), static_cast<char *>(seg1.p)};
     // images after steps k0 .. k1-2 of segment si into segs[si & 1]: each step
     // reads the image before it (the checkpoint first) and writes the next
+    // (the image step takes memory variables in the state type: FP32 or FP64
+    // storage, the only ones fw_gradient accepts)
     auto recompute = [&](int si) -> int {
         const int k0 = si * K, k1 = std::min(n_steps, k0 + K);
         const char *rd = static_cast<const char *>(ck.p) + (size_t)si * SB;

@@ -1057,7 +1057,9 @@ int fw_set_sources(fw_medium *m, const uint8_t *mask, const float *waveforms, in
     m->src_rcv = nullptr;
     m->n_src = 0;
     m->h_src_idx.clear();
-    if (ns == 0) return upload_io_map(m, s);
+    // receivers stop pointing at the old sources before anything can fail
+    if (int rc = upload_io_map(m, s)) return rc;
+    if (ns == 0) return FW_OK;
     const size_t wl = (size_t)n_wave * n_steps;
     const size_t o_idx = 0, o_gain = align_up(ns * 8, 256), o_wof = o_gain + align_up((size_t)ns * m->es, 256),
                  o_map = o_wof + align_up((size_t)ns * 4, 256), o_wave = o_map + align_up((size_t)ns * 4, 256),
@@ -1109,8 +1111,10 @@ int fw_set_receivers(fw_medium *m, const uint8_t *mask, int decim, int n_steps)
     m->n_rcv = 0;
     m->n_rec = 0;
     m->h_rcv_idx.clear();
+    // sources stop pointing at the old receivers before anything can fail
+    if (int rc = upload_io_map(m, s)) return rc;
     const int nr = (int)idx.size();
-    if (nr == 0) return upload_io_map(m, s);
+    if (nr == 0) return FW_OK;
     const int nrec = (n_steps + decim - 1) / decim;
     const size_t o_map = align_up((size_t)nr * 8, 256), o_tr = o_map + align_up((size_t)nr * 4, 256),
                  total = o_tr + align_up((size_t)nr * std::max(nrec, 1) * m->es, 256);
