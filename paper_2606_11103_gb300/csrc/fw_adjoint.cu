@@ -744,7 +744,8 @@ __device__ __forceinline__ void step2_tile(const AdjArgs<R> &A, unsigned char *s
 
 // Tiles whose reads (the q_d halo reaches 7 cells, one more for the velocity
 // adjoint's neighbouring density) stay clear of the absorbing layer take the
-// PLAIN instance: no layer memory, tissue strength 1.
+// PLAIN instance: no layer memory, tissue strength 1.  Registers are held
+// to four CTAs per SM (64 per thread) in FP32, two in FP64.
 template <typename R, int NM, int TX, int TZ>
 __global__ void __launch_bounds__(kAdjThreads, sizeof(R) == 4 ? 4 : 2) k_adj_step2(const AdjArgs<R> A)
 {
